@@ -1,0 +1,162 @@
+/* polymul.h -- C-ABI of the GB300 sparse multivariate polynomial product.
+ *
+ * The library computes the exact schoolbook product h = f * g of two sparse
+ * multivariate polynomials held in distributed format: a list of terms, each
+ * a coefficient with an exponent vector (Gastineau & Laskar, "Highly Scalable
+ * Multiplication for Distributed Sparse Multivariate Polynomials on Many-core
+ * Systems", Sec. 1 and Sec. 2).  Every pairwise term product
+ * a_i b_j x^(alpha_i + beta_j) is formed and equal monomials are combined
+ * into a result sorted in ascending monomial order (Sec. 2, Alg. 1).
+ *
+ * All compute runs in the library's CUDA kernels for sm_103a.  Every pointer
+ * named "device" below must be device memory of the current CUDA device (for
+ * example a PyTorch CUDA tensor's data pointer); the library never frees
+ * caller memory.  `stream` is a cudaStream_t passed as void* (NULL = the
+ * legacy default stream); all work is ordered on it.  Calls return only after
+ * the result is complete and its size is known on the host.
+ *
+ * Monomial order: lexicographic with x_1 most significant.  Exponents are
+ * packed into one 64-bit key (Sec. 7: "packed on a 64-bit unsigned
+ * integer"): x_1 occupies the most significant field.  Each field's width
+ * counts one guard bit (the field's top bit): every exponent must be
+ * < 2^(w_v - 1), so adding two packed keys never carries between fields and
+ * multiplying two monomials is one integer add.
+ *
+ * Coefficient rings:
+ *   PM_COEF_M61        uint64 inputs (any value, reduced mod p on load),
+ *                      results in [0, p), p = 2^61 - 1.
+ *   PM_COEF_I64_ACC128 int64 inputs, exact results as int128 stored as two
+ *                      uint64 words per term (low word first, two's
+ *                      complement).
+ *
+ * Input conventions: terms in any order; a repeated monomial's coefficients
+ * are summed; zero coefficients are dropped.  The result never holds a zero
+ * coefficient or a repeated monomial (the canonical form of Sec. 2).
+ */
+#ifndef POLYMUL_H
+#define POLYMUL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PM_MAX_VARS 16
+
+/* ---- error codes (negative) ---------------------------------------------- */
+#define PM_OK             0
+#define PM_EINVAL        -1  /* bad packing, kind, pointer or size              */
+#define PM_EEXP_OVERFLOW -2  /* an input or product exponent reaches its guard  */
+#define PM_ECOEF_BOUND   -3  /* int64 kind: the int128 bound rule fails         */
+#define PM_ECAPACITY     -4  /* h->cap too small; h->n holds the needed size    */
+#define PM_ENOMEM        -5  /* device scratch allocation failed                */
+#define PM_ETIMEOUT      -6  /* a bounded device wait gave up                   */
+#define PM_ECUDA         -7  /* a CUDA runtime call failed                      */
+
+/* ---- types ---------------------------------------------------------------- */
+
+/* Exponent packing: nvars in [1, 16]; field_bits[v] in [1, 32] is the width
+ * of x_{v+1}'s field including its guard bit; the widths sum to <= 64. */
+typedef struct pm_packing {
+    uint32_t nvars;
+    uint8_t field_bits[PM_MAX_VARS];
+} pm_packing;
+
+typedef enum pm_coef_kind {
+    PM_COEF_M61 = 0,
+    PM_COEF_I64_ACC128 = 1
+} pm_coef_kind;
+
+/* Input terms (device): exps is n x nvars uint32, row-major; coefs is n
+ * uint64 (M61) or n int64 (I64_ACC128).  n < 2^31. */
+typedef struct pm_terms_in {
+    const uint32_t *exps;
+    const void *coefs;
+    uint64_t n;
+} pm_terms_in;
+
+/* Output terms (device): keys is cap packed uint64 keys; coefs is cap uint64
+ * (M61) or 2*cap uint64 words (I64_ACC128).  On success n = number of terms
+ * written.  On PM_ECAPACITY n = the number of terms the result has. */
+typedef struct pm_terms_out {
+    uint64_t *keys;
+    void *coefs;
+    uint64_t n;
+    uint64_t cap;
+} pm_terms_out;
+
+/* Strategies for the per-range accumulate step. */
+#define PM_STRATEGY_AUTO   0  /* autotuner's choice (default)                      */
+#define PM_STRATEGY_DIRECT 1  /* direct-addressed shared-memory accumulation       */
+#define PM_STRATEGY_SORT   2  /* shared-memory radix sort + segmented reduce       */
+
+/* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
+typedef struct pm_options {
+    int32_t strategy;          /* PM_STRATEGY_*                                   */
+    uint32_t slots;            /* direct: output slots per range (<= 24576)        */
+    uint32_t chunk;            /* sort: term products per range (<= 4096)          */
+    uint32_t ranges_per_sm;    /* load-balance target: ranges per SM               */
+} pm_options;
+
+/* Per-call counters (all optional; pass NULL). */
+typedef struct pm_stats {
+    uint64_t n_f, n_g;         /* canonical operand sizes                         */
+    uint64_t term_products;    /* n_f * n_g                                       */
+    uint64_t n_out;            /* result terms                                    */
+    uint64_t n_ranges;         /* output key ranges (one CTA each)                */
+    uint64_t box;              /* output-exponent box size used for ranks          */
+    int32_t strategy;          /* PM_STRATEGY_DIRECT or PM_STRATEGY_SORT          */
+    uint32_t refine_rounds;    /* partition refinement rounds                      */
+    uint32_t kernel_launches;  /* kernels launched by the call                     */
+    uint32_t host_syncs;       /* stream synchronisations by the call              */
+    float ms_range_kernel;     /* device time of the accumulate kernel (ms)        */
+} pm_stats;
+
+/* ---- entry points ---------------------------------------------------------- */
+
+/* h = f * g (Sec. 2, Alg. 1).  Steps, all on the device:
+ *   (a) pack exponents into guard-bit keys, reduce coefficients, sort each
+ *       operand and combine repeated monomials (Sec. 7 packing);
+ *   (b) split the output key space into disjoint left-closed, right-open
+ *       ranges [S_k, S_{k+1}) whose term-product counts O_k are balanced
+ *       (Sec. 2 first step, Sec. 3 operation counts);
+ *   (c)+(d) one CTA per range forms its term products from per-row column
+ *       bounds (FindEdge, Sec. 2) and accumulates them in shared memory,
+ *       with no atomics or locks on the result (Alg. 1 second step);
+ *   (e) drops zero coefficients and concatenates the ranges in ascending
+ *       order (Alg. 1, last line).
+ * Errors: PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND (int64 kind: a
+ * repeated input monomial's sum leaves int64, or
+ * max|a| * max|b| * min(n_f, n_g) >= 2^127 over the canonical operands),
+ * PM_ECAPACITY (h->n set to the needed size), PM_ENOMEM, PM_ECUDA.  On any
+ * error h's buffers hold unspecified data and h->n = 0 except for
+ * PM_ECAPACITY.  Scratch memory comes from the device's stream-ordered
+ * allocator and is released before return. */
+int pm_polymul(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+               pm_terms_out *h, const pm_options *opt, pm_stats *stats, void *stream);
+
+/* Upper bound on the number of result terms: min(n_f * n_g, box) with box =
+ * prod_v (max_f e_v + max_g e_v + 1) over the input terms.  Sizes h->cap. */
+int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g,
+                 uint64_t *bound, void *stream);
+
+/* Unpack n packed keys (device) into an n x nvars uint32 exponent matrix
+ * (device, row-major).  Inverse of the packing of Sec. 7. */
+int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *exps, void *stream);
+
+/* Pack n exponent vectors (device, n x nvars uint32) into keys (device).
+ * Fails with PM_EEXP_OVERFLOW if an exponent reaches its guard bit. */
+int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream);
+
+/* Human-readable message for an error code (static storage). */
+const char *pm_strerror(int code);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int pm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,20 @@
+"""GB300 (sm_103a) exact sparse multivariate polynomial product.
+
+The compute lives in libpolymul.so (CUDA kernels behind the C-ABI of
+include/polymul.h); this package is its thin Python binding.  Importing the
+package loads nothing; the first call loads the library and raises if it is
+missing.
+"""
+
+from ._native import (  # noqa: F401
+    PolymulError,
+    Product,
+    SYMBOLS,
+    lib,
+    out_bound,
+    pack,
+    polymul,
+    unpack,
+)
+
+__all__ = ["polymul", "unpack", "pack", "out_bound", "PolymulError", "Product", "lib", "SYMBOLS"]

@@ -1,0 +1,218 @@
+"""ctypes binding of libpolymul.so (include/polymul.h).
+
+Argument marshalling only: tensors are passed to the C-ABI as raw device
+pointers with the current CUDA stream; every step of the product runs in the
+library's kernels.  There is no fallback: if the library is missing or no
+CUDA device is present the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpolymul.so")
+
+PM_MAX_VARS = 16
+PM_OK, PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND = 0, -1, -2, -3
+PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA = -4, -5, -6, -7
+KIND = {"m61": 0, "i64": 1}
+STRATEGY = {"auto": 0, "direct": 1, "sort": 2}
+STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
+
+
+class pm_packing(C.Structure):
+    _fields_ = [("nvars", C.c_uint32), ("field_bits", C.c_uint8 * PM_MAX_VARS)]
+
+
+class pm_terms_in(C.Structure):
+    _fields_ = [("exps", C.c_void_p), ("coefs", C.c_void_p), ("n", C.c_uint64)]
+
+
+class pm_terms_out(C.Structure):
+    _fields_ = [("keys", C.c_void_p), ("coefs", C.c_void_p), ("n", C.c_uint64), ("cap", C.c_uint64)]
+
+
+class pm_options(C.Structure):
+    _fields_ = [("strategy", C.c_int32), ("slots", C.c_uint32), ("chunk", C.c_uint32),
+                ("ranges_per_sm", C.c_uint32)]
+
+
+class pm_stats(C.Structure):
+    _fields_ = [("n_f", C.c_uint64), ("n_g", C.c_uint64), ("term_products", C.c_uint64),
+                ("n_out", C.c_uint64), ("n_ranges", C.c_uint64), ("box", C.c_uint64),
+                ("strategy", C.c_int32), ("refine_rounds", C.c_uint32),
+                ("kernel_launches", C.c_uint32), ("host_syncs", C.c_uint32),
+                ("ms_range_kernel", C.c_float)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["strategy"] = STRATEGY_NAME.get(d["strategy"], d["strategy"])
+        return d
+
+
+class PolymulError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        msg = lib().pm_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+        self.code = code
+
+
+# exported symbols, in include/polymul.h order
+SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_strerror", "pm_version")
+
+_lib = None
+
+
+def lib():
+    """Load libpolymul.so (no compute call is made here)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_1303_7425_gb300.build.build() first")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        L.pm_polymul.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), P(pm_terms_out),
+                                 P(pm_options), P(pm_stats), C.c_void_p]
+        L.pm_polymul.restype = C.c_int
+        L.pm_out_bound.argtypes = [P(pm_packing), P(pm_terms_in), P(pm_terms_in), P(C.c_uint64), C.c_void_p]
+        L.pm_out_bound.restype = C.c_int
+        L.pm_unpack.argtypes = [P(pm_packing), C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
+        L.pm_unpack.restype = C.c_int
+        L.pm_pack.argtypes = [P(pm_packing), C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
+        L.pm_pack.restype = C.c_int
+        L.pm_strerror.argtypes = [C.c_int]
+        L.pm_strerror.restype = C.c_char_p
+        L.pm_version.argtypes = []
+        L.pm_version.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def packing(field_bits: Sequence[int]) -> pm_packing:
+    pk = pm_packing()
+    pk.nvars = len(field_bits)
+    for v, w in enumerate(field_bits[:PM_MAX_VARS]):
+        pk.field_bits[v] = int(w)
+    return pk
+
+
+def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0) -> pm_options:
+    o = pm_options()
+    o.strategy = STRATEGY[strategy]
+    o.slots = slots
+    o.chunk = chunk
+    o.ranges_per_sm = ranges_per_sm
+    return o
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _terms_in(exps, coefs) -> pm_terms_in:
+    t = pm_terms_in()
+    n = int(exps.shape[0])
+    t.n = n
+    t.exps = exps.data_ptr() if n else None
+    t.coefs = coefs.data_ptr() if n else None
+    return t
+
+
+def _check_cuda(*tensors):
+    for x in tensors:
+        if not x.is_cuda:
+            raise ValueError("inputs must be CUDA tensors")
+        if not x.is_contiguous():
+            raise ValueError("inputs must be contiguous")
+
+
+@dataclass
+class Product:
+    keys: "object"            # (n,) int64 tensor holding uint64 packed keys
+    coefs: "object"           # (n,) int64 tensor of residues, or (n, 2) int128 (lo, hi) words
+    n: int
+    stats: dict
+
+
+def out_bound(field_bits, f_exps, g_exps, stream=None) -> int:
+    _check_cuda(f_exps, g_exps)
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_exps)
+    g = _terms_in(g_exps, g_exps)
+    b = C.c_uint64(0)
+    rc = lib().pm_out_bound(C.byref(pk), C.byref(f), C.byref(g), C.byref(b), _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_out_bound")
+    return int(b.value)
+
+
+def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61",
+            strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
+            out=None, stream=None) -> Product:
+    """h = f * g on the current CUDA device.
+
+    f_exps/g_exps: (n, nvars) int32/uint32 CUDA tensors; f_coefs/g_coefs: (n,)
+    int64/uint64 CUDA tensors.  ``out``: optional (keys, coefs) tensors to
+    write into (their length is the capacity); otherwise they are allocated
+    from pm_out_bound."""
+    import torch
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
+    words = 1 if kind == "m61" else 2
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    if out is None:
+        cap = out_bound(field_bits, f_exps, g_exps, stream)
+        keys = torch.empty(max(cap, 1), dtype=torch.int64, device=f_exps.device)
+        coefs = torch.empty((max(cap, 1), 2) if words == 2 else (max(cap, 1),), dtype=torch.int64,
+                            device=f_exps.device)
+    else:
+        keys, coefs = out
+        cap = int(keys.shape[0])
+    h = pm_terms_out()
+    h.keys = keys.data_ptr()
+    h.coefs = coefs.data_ptr()
+    h.cap = cap
+    st = pm_stats()
+    o = options(strategy, slots, chunk, ranges_per_sm)
+    rc = lib().pm_polymul(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(o),
+                          C.byref(st), _stream_handle(stream))
+    if rc != PM_OK:
+        err = PolymulError(rc, "pm_polymul")
+        err.needed = int(h.n)
+        raise err
+    n = int(h.n)
+    return Product(keys[:n], coefs[:n], n, st.as_dict())
+
+
+def unpack(field_bits: Sequence[int], keys, stream=None):
+    """(n,) packed keys -> (n, nvars) int32 exponent tensor."""
+    import torch
+    _check_cuda(keys)
+    n = int(keys.shape[0])
+    exps = torch.empty((n, len(field_bits)), dtype=torch.int32, device=keys.device)
+    if n:
+        rc = lib().pm_unpack(C.byref(packing(field_bits)), keys.data_ptr(), n, exps.data_ptr(),
+                             _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_unpack")
+    return exps
+
+
+def pack(field_bits: Sequence[int], exps, stream=None):
+    import torch
+    _check_cuda(exps)
+    n = int(exps.shape[0])
+    keys = torch.empty(max(n, 1), dtype=torch.int64, device=exps.device)
+    if n:
+        rc = lib().pm_pack(C.byref(packing(field_bits)), exps.data_ptr(), n, keys.data_ptr(),
+                           _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_pack")
+    return keys[:n]

@@ -1,0 +1,419 @@
+// Host driver and C-ABI entry points (include/polymul.h).
+//
+// pm_polymul runs Alg. 1 of the paper on one GPU: K-a canonical operands,
+// K-b output ranges with balanced operation counts, K-c/K-d one CTA per range,
+// K-e concatenation.  The host only reads sizes and status words between
+// steps; every array the product touches is processed by the kernels.
+#include <cstring>
+#include <mutex>
+
+#include "pm_pack.cuh"
+#include "pm_partition.cuh"
+#include "pm_range.cuh"
+
+namespace pm {
+
+constexpr u32 DEFAULT_SLOTS = 24576;   // direct: 192 KB of 64-bit accumulators
+constexpr u32 MAX_SLOTS = 24576;
+constexpr u32 DEFAULT_CHUNK = 4096;    // sort: term products per range
+constexpr u32 MAX_CHUNK = 4096;
+constexpr u32 DEFAULT_RANGES_PER_SM = 4;
+
+// K-e: copy each range's terms from its scratch slice to its final place
+__global__ void k_compact_copy(const u64 *__restrict__ skey, const u64 *__restrict__ scoef,
+                               const u64 *__restrict__ boff, const u64 *__restrict__ foff,
+                               const u64 *__restrict__ ucount, u32 nranges, u32 words, u64 *__restrict__ hkey,
+                               u64 *__restrict__ hcoef)
+{
+    for (u32 k = blockIdx.x; k < nranges; k += gridDim.x) {
+        const u64 src = boff[k], dst = foff[k], n = ucount[k];
+        for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
+            hkey[dst + t] = skey[src + t];
+            if (words == 1) {
+                hcoef[dst + t] = scoef[src + t];
+            } else {
+                hcoef[2 * (dst + t)] = scoef[2 * (src + t)];
+                hcoef[2 * (dst + t) + 1] = scoef[2 * (src + t) + 1];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+
+static std::mutex g_dev_mu;
+static int g_sm_count[64];
+static bool g_pool_ready[64];
+
+static void device_setup(Ctx &c)
+{
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (dev < 64 && g_pool_ready[dev]) {
+        c.sm_count = g_sm_count[dev];
+        return;
+    }
+    int sms = 0;
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // keep freed scratch in this process's pool between calls
+    cudaMemPool_t pool;
+    PM_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t thr = ~0ull;
+    PM_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    if (dev < 64) {
+        g_sm_count[dev] = sms;
+        g_pool_ready[dev] = true;
+    }
+    c.sm_count = sms;
+}
+
+static void validate_packing(const pm_packing *pk)
+{
+    if (!pk || pk->nvars < 1 || pk->nvars > PM_MAX_VARS) throw Error(PM_EINVAL, "bad nvars");
+    u32 sum = 0;
+    for (u32 v = 0; v < pk->nvars; v++) {
+        if (pk->field_bits[v] < 1 || pk->field_bits[v] > 32) throw Error(PM_EINVAL, "bad field width");
+        sum += pk->field_bits[v];
+    }
+    if (sum > 64) throw Error(PM_EINVAL, "fields exceed 64 bits");
+}
+
+static void validate_terms(const pm_terms_in *t)
+{
+    if (!t) throw Error(PM_EINVAL, "null operand");
+    if (t->n >= (1ull << 31)) throw Error(PM_EINVAL, "operand too large");
+    if (t->n && (!t->exps || !t->coefs)) throw Error(PM_EINVAL, "null operand arrays");
+}
+
+static Layout base_layout(const pm_packing &pk)
+{
+    Layout L;
+    memset(&L, 0, sizeof(L));
+    L.nv = pk.nvars;
+    u32 s = 0;
+    for (int v = (int)pk.nvars - 1; v >= 0; v--) {
+        L.off[v] = s;
+        L.width[v] = pk.field_bits[v];
+        s += pk.field_bits[v];
+    }
+    return L;
+}
+
+// extents E_v = mf_v + mg_v + 1; strides of the mixed radix with x_1 most
+// significant; returns the box size prod E_v (< 2^64 under the guard rule)
+static u64 set_box(Layout &L, const u32 *mf, const u32 *mg)
+{
+    u64 stride = 1;
+    for (int v = (int)L.nv - 1; v >= 0; v--) {
+        L.extent[v] = (u64)mf[v] + mg[v] + 1;
+        L.stride[v] = stride;
+        stride *= L.extent[v];
+    }
+    return stride;
+}
+
+struct Small {  // host mirror of the small device block
+    u32 status;
+    u32 maxe_f[PM_MAX_VARS], maxe_g[PM_MAX_VARS];
+    u32 pad;
+    u64 count_f, count_g, maxabs_f, maxabs_g;
+};
+
+static void read_small(Ctx &c, Small &h, const Small *d)
+{
+    PM_CUDA(cudaMemcpyAsync(&h, d, sizeof(Small), cudaMemcpyDeviceToHost, c.s));
+    c.sync();
+}
+
+static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, const pm_terms_in *g,
+                        pm_terms_out *h, const pm_options *opt, pm_stats *st, cudaStream_t stream)
+{
+    validate_packing(pk);
+    if (kind != PM_COEF_M61 && kind != PM_COEF_I64_ACC128) throw Error(PM_EINVAL, "bad coefficient kind");
+    validate_terms(f);
+    validate_terms(g);
+    if (!h) throw Error(PM_EINVAL, "null output");
+    if (h->cap && (!h->keys || !h->coefs)) throw Error(PM_EINVAL, "null output arrays");
+    h->n = 0;
+    pm_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.slots > MAX_SLOTS || o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2)
+        throw Error(PM_EINVAL, "bad options");
+    pm_stats stats;
+    memset(&stats, 0, sizeof(stats));
+
+    Ctx c;
+    c.s = stream;
+    device_setup(c);
+    Scratch S(stream);
+    Small hs;
+    Small *ds = S.get<Small>(1);
+    PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
+
+    // K-a (1): input guard bits and the raw exponent box
+    Layout L = base_layout(*pk);
+    input_maxima(c, *f, L, ds->maxe_f, &ds->status);
+    input_maxima(c, *g, L, ds->maxe_g, &ds->status);
+    read_small(c, hs, ds);
+    if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
+    auto finish_empty = [&]() {
+        h->n = 0;
+        if (st) {
+            stats.kernel_launches = c.launches;
+            stats.host_syncs = c.syncs;
+            *st = stats;
+        }
+        return PM_OK;
+    };
+    if (f->n == 0 || g->n == 0) return finish_empty();
+    Layout raw = L;
+    const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
+
+    // K-a (2): canonical operands
+    Operand F, G;
+    canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
+    canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
+    PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * 2 * PM_MAX_VARS, c.s));
+    read_small(c, hs, ds);
+    if (hs.status & ST_COEF_BOUND) throw Error(PM_ECOEF_BOUND, "repeated input monomial leaves int64");
+    F.n = hs.count_f;
+    G.n = hs.count_g;
+    stats.n_f = F.n;
+    stats.n_g = G.n;
+    if (F.n == 0 || G.n == 0) return finish_empty();
+
+    // K-a (3): exponent-sum guard, int128 bound, the product's box
+    operand_stats(c, F, L, kind, ds->maxe_f, &ds->maxabs_f);
+    operand_stats(c, G, L, kind, ds->maxe_g, &ds->maxabs_g);
+    read_small(c, hs, ds);
+    for (u32 v = 0; v < L.nv; v++)
+        if ((u64)hs.maxe_f[v] + hs.maxe_g[v] >= (1ull << (L.width[v] - 1)))
+            throw Error(PM_EEXP_OVERFLOW, "product exponent reaches its guard bit");
+    if (kind == PM_COEF_I64_ACC128) {
+        unsigned __int128 m = (unsigned __int128)hs.maxabs_f * hs.maxabs_g;
+        unsigned __int128 lim = ((((unsigned __int128)1) << 127) - 1) / (F.n < G.n ? F.n : G.n);
+        if (m > lim) throw Error(PM_ECOEF_BOUND, "int128 bound rule fails");
+    }
+    const u64 box = set_box(L, hs.maxe_f, hs.maxe_g);
+    const u64 products = F.n * G.n;
+    stats.term_products = products;
+    stats.box = box;
+
+    // strategy (autotuner defaults; see pm_tune)
+    int strategy = o.strategy;
+    const u32 slots_max = kind == PM_COEF_M61 ? MAX_SLOTS : MAX_SLOTS / 2;
+    u32 slots = o.slots ? o.slots : DEFAULT_SLOTS;
+    if (slots > slots_max) slots = slots_max;
+    const u32 chunk = o.chunk ? o.chunk : DEFAULT_CHUNK;
+    const u32 rps = o.ranges_per_sm ? o.ranges_per_sm : DEFAULT_RANGES_PER_SM;
+    if (strategy == PM_STRATEGY_AUTO) {
+        bool dense = box <= 16 * products && box / slots < (1ull << 22);
+        strategy = dense ? PM_STRATEGY_DIRECT : PM_STRATEGY_SORT;
+    }
+    if (strategy == PM_STRATEGY_DIRECT && box / slots >= (1ull << 23))
+        throw Error(PM_EINVAL, "exponent box too large for the direct strategy");
+    stats.strategy = strategy;
+
+    // K-b: output ranges
+    PartitionPlan plan;
+    const u64 *A, *B;
+    if (strategy == PM_STRATEGY_DIRECT) {
+        operand_ranks(c, F, L);
+        operand_ranks(c, G, L);
+        A = F.rank;
+        B = G.rank;
+        plan.uniform_step = slots;
+        u64 tgt = products / ((u64)rps * c.sm_count);
+        plan.target = tgt < 32768 ? 32768 : tgt;
+        plan.hard_target = false;
+        plan.max_rounds = 4;
+    } else {
+        A = F.key;
+        B = G.key;
+        double want = 4.0 * (double)products / chunk;
+        u32 l = 1;
+        while ((double)(l + 1) * (l + 1) < want && l < 2048) l++;
+        plan.grid_l = l;
+        plan.target = chunk;
+        plan.hard_target = true;
+        plan.max_rounds = 64;
+    }
+    Ranges R = partition(c, S, A, (u32)F.n, B, (u32)G.n, plan);
+    stats.n_ranges = R.n;
+    stats.refine_rounds = R.rounds;
+
+    // K-c/K-d: one CTA per range
+    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
+    RangeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.fkey = A;
+    a.fcoef = F.coef;
+    a.gkey = B;
+    a.gcoef = G.coef;
+    a.na = (u32)F.n;
+    a.nb = (u32)G.n;
+    a.rlo = R.lo;
+    a.rhi = R.hi;
+    a.rO = R.O;
+    a.boff = R.boff;
+    a.nranges = R.n;
+    a.okey = S.get<u64>(R.out_bound + 1);
+    a.ocoef = S.get<u64>((R.out_bound + 1) * words);
+    a.ucount = S.get<u64>(R.n + 1);
+    a.L = L;
+    a.status = &ds->status;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st) {
+        PM_CUDA(cudaEventCreate(&e0));
+        PM_CUDA(cudaEventCreate(&e1));
+        PM_CUDA(cudaEventRecord(e0, c.s));
+    }
+    if (R.n) {
+        if (strategy == PM_STRATEGY_DIRECT) launch_range_direct(c, a, slots, kind, R.n);
+        else launch_range_sort(c, a, chunk, kind, R.n);
+    }
+    if (st) PM_CUDA(cudaEventRecord(e1, c.s));
+
+    // K-e: concatenate the ranges in ascending order
+    u64 *foff = S.get<u64>(R.n + 1);
+    scan_exclusive_u64(c, S, a.ucount, foff, R.n);
+    u64 n_out = 0;
+    PM_CUDA(cudaMemcpyAsync(&n_out, foff + R.n, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
+    PM_CUDA(cudaMemcpyAsync(&hs.status, &ds->status, sizeof(u32), cudaMemcpyDeviceToHost, c.s));
+    c.sync();
+    if (st) {
+        PM_CUDA(cudaEventElapsedTime(&stats.ms_range_kernel, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    if (hs.status & ST_INTERNAL) throw Error(PM_ECUDA, "internal consistency check failed");
+    stats.n_out = n_out;
+    if (n_out > h->cap) {
+        h->n = n_out;
+        if (st) *st = stats;
+        return PM_ECAPACITY;
+    }
+    if (R.n && n_out) {
+        unsigned grid = R.n < 65535u ? R.n : 65535u;
+        k_compact_copy<<<grid, 256, 0, c.s>>>(a.okey, a.ocoef, R.boff, foff, a.ucount, R.n, words, (u64 *)h->keys,
+                                              (u64 *)h->coefs);
+        PM_LAUNCHED(c);
+    }
+    h->n = n_out;
+    if (st) {
+        stats.kernel_launches = c.launches;
+        stats.host_syncs = c.syncs;
+        *st = stats;
+    }
+    return PM_OK;
+}
+
+}  // namespace pm
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+
+using namespace pm;
+
+template <class F>
+static int guarded(F &&fn)
+{
+    try {
+        return fn();
+    } catch (const Error &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return PM_ENOMEM;
+    } catch (...) {
+        return PM_ECUDA;
+    }
+}
+
+extern "C" int pm_polymul(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                          pm_terms_out *h, const pm_options *opt, pm_stats *stats, void *stream)
+{
+    int rc = guarded([&] { return polymul_impl(pk, coef_kind, f, g, h, opt, stats, (cudaStream_t)stream); });
+    if (rc != PM_OK && rc != PM_ECAPACITY && h) h->n = 0;
+    return rc;
+}
+
+extern "C" int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, uint64_t *bound,
+                            void *stream)
+{
+    return guarded([&] {
+        validate_packing(pk);
+        validate_terms(f);
+        validate_terms(g);
+        if (!bound) throw Error(PM_EINVAL, "null bound");
+        *bound = 0;
+        if (f->n == 0 || g->n == 0) return PM_OK;
+        Ctx c;
+        c.s = (cudaStream_t)stream;
+        device_setup(c);
+        Scratch S(c.s);
+        Small hs;
+        Small *ds = S.get<Small>(1);
+        PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
+        Layout L = base_layout(*pk);
+        input_maxima(c, *f, L, ds->maxe_f, &ds->status);
+        input_maxima(c, *g, L, ds->maxe_g, &ds->status);
+        read_small(c, hs, ds);
+        if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
+        u64 box = set_box(L, hs.maxe_f, hs.maxe_g);
+        unsigned __int128 prod = (unsigned __int128)f->n * g->n;
+        *bound = prod < box ? (u64)prod : box;
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *exps, void *stream)
+{
+    return guarded([&] {
+        validate_packing(pk);
+        if (n && (!keys || !exps)) throw Error(PM_EINVAL, "null arrays");
+        Ctx c;
+        c.s = (cudaStream_t)stream;
+        unpack_keys(c, (const u64 *)keys, n, base_layout(*pk), exps);
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream)
+{
+    return guarded([&] {
+        validate_packing(pk);
+        if (n && (!keys || !exps)) throw Error(PM_EINVAL, "null arrays");
+        if (n == 0) return PM_OK;
+        Ctx c;
+        c.s = (cudaStream_t)stream;
+        Scratch S(c.s);
+        u32 *st = S.get<u32>(1);
+        PM_CUDA(cudaMemsetAsync(st, 0, sizeof(u32), c.s));
+        pack_keys(c, exps, n, base_layout(*pk), (u64 *)keys, st);
+        u32 hst = 0;
+        PM_CUDA(cudaMemcpyAsync(&hst, st, sizeof(u32), cudaMemcpyDeviceToHost, c.s));
+        c.sync();
+        if (hst & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "exponent reaches its guard bit");
+        return PM_OK;
+    });
+}
+
+extern "C" const char *pm_strerror(int code)
+{
+    switch (code) {
+    case PM_OK: return "success";
+    case PM_EINVAL: return "invalid argument";
+    case PM_EEXP_OVERFLOW: return "exponent reaches its field's guard bit";
+    case PM_ECOEF_BOUND: return "int128 coefficient bound rule fails";
+    case PM_ECAPACITY: return "output capacity too small";
+    case PM_ENOMEM: return "device memory allocation failed";
+    case PM_ETIMEOUT: return "bounded device wait timed out";
+    case PM_ECUDA: return "CUDA runtime error";
+    default: return "unknown error";
+    }
+}
+
+extern "C" int pm_version(void) { return 100; }

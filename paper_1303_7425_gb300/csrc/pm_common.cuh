@@ -1,0 +1,258 @@
+// Shared device helpers of the polymul library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "polymul.h"
+
+namespace pm {
+
+typedef unsigned long long u64;
+typedef long long i64;
+typedef unsigned int u32;
+
+constexpr u64 P61 = 0x1FFFFFFFFFFFFFFFull;  // 2^61 - 1
+
+// status bits written by kernels, read by the host at the end of a step
+constexpr u32 ST_EXP_OVERFLOW = 1u;
+constexpr u32 ST_COEF_BOUND = 2u;
+constexpr u32 ST_CAPACITY = 4u;
+constexpr u32 ST_INTERNAL = 8u;
+
+// ---------------------------------------------------------------------------
+// arithmetic mod p = 2^61 - 1.  2^61 = 1 (mod p), so a 122-bit product
+// hi * 2^64 + lo splits into (bits >= 61) + (bits < 61) with one add.
+// ---------------------------------------------------------------------------
+
+// a, b < 2^61: returns r < 2^62 with r = a*b (mod p)
+__device__ __forceinline__ u64 m61_mul_lazy(u64 a, u64 b)
+{
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    return (lo & P61) + ((hi << 3) | (lo >> 61));
+}
+
+// any 64-bit x -> [0, p)
+__device__ __forceinline__ u64 m61_reduce(u64 x)
+{
+    u64 r = (x & P61) + (x >> 61);  // <= p + 7
+    return r >= P61 ? r - P61 : r;
+}
+
+// a, b in [0, p) -> a + b mod p
+__device__ __forceinline__ u64 m61_add(u64 a, u64 b)
+{
+    u64 r = a + b;
+    return r >= P61 ? r - P61 : r;
+}
+
+// 2^64 = 2^3 * 2^61 = 8 (mod p): adding into a wrapping 64-bit word stays
+// exact mod p if every wrap is followed by an add of 8.
+__device__ __forceinline__ void m61_atomic_accumulate(u64 *slot, u64 v)
+{
+    u64 old = atomicAdd(slot, v);
+    u64 add = (old + v < old) ? 8ull : 0ull;
+    while (add) {
+        old = atomicAdd(slot, add);
+        add = (old + add < old) ? 8ull : 0ull;
+    }
+}
+
+// signed 64 x 64 -> 128 product as (lo, hi) words
+__device__ __forceinline__ void mul_i64_wide(i64 a, i64 b, u64 &lo, u64 &hi)
+{
+    lo = (u64)a * (u64)b;
+    hi = (u64)__mul64hi(a, b);
+}
+
+__device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 blo, u64 bhi)
+{
+    u64 l = lo + blo;
+    hi = hi + bhi + (l < lo ? 1ull : 0ull);
+    lo = l;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide exclusive scan (all threads of the block must call it)
+// ---------------------------------------------------------------------------
+
+// one value per thread; returns the thread's exclusive prefix and sets
+// `total` to the block's sum.  warp_sums: 32 words of shared memory.
+__device__ __forceinline__ u64 block_exclusive_scan(u64 v, u64 &total, u64 *warp_sums)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        u64 y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        u64 s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            u64 y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        if (lane < nw) warp_sums[lane] = s;  // inclusive over warps
+    }
+    __syncthreads();
+    u64 wbase = w > 0 ? warp_sums[w - 1] : 0;
+    total = warp_sums[nw - 1];
+    __syncthreads();
+    return wbase + x - v;
+}
+
+// ---------------------------------------------------------------------------
+// searches over sorted uint64 arrays
+// ---------------------------------------------------------------------------
+
+// first index i in [0, n) with a[i] >= x (n if none)
+__device__ __forceinline__ u32 lower_bound_u64(const u64 *__restrict__ a, u32 n, u64 x)
+{
+    u32 lo = 0, len = n;
+    while (len > 0) {
+        u32 half = len >> 1;
+        if (__ldg(a + lo + half) < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// exponent layout passed by value to kernels
+// ---------------------------------------------------------------------------
+
+struct Layout {
+    u32 nv;
+    u32 off[PM_MAX_VARS];     // bit offset of x_v's field (x_1 most significant)
+    u32 width[PM_MAX_VARS];   // field width incl. guard bit
+    u64 stride[PM_MAX_VARS];  // mixed-radix stride of x_v in the rank box
+    u64 extent[PM_MAX_VARS];  // rank box extent of x_v
+};
+
+__device__ __forceinline__ u32 key_field(const Layout &L, u64 key, u32 v)
+{
+    return (u32)((key >> L.off[v]) & ((1ull << L.width[v]) - 1ull));
+}
+
+__device__ __forceinline__ u64 key_to_rank(const Layout &L, u64 key)
+{
+    u64 r = 0;
+    for (u32 v = 0; v < L.nv; v++) r += (u64)key_field(L, key, v) * L.stride[v];
+    return r;
+}
+
+// rank -> packed key, for ranks inside the box
+__device__ __forceinline__ u64 rank_to_key(const Layout &L, u64 rank)
+{
+    u64 key = 0;
+    if (rank <= 0xFFFFFFFFull) {
+        u32 r = (u32)rank;
+        for (int v = (int)L.nv - 1; v >= 0; v--) {
+            u32 e = (u32)L.extent[v];
+            u32 q = r / e;
+            key |= (u64)(r - q * e) << L.off[v];
+            r = q;
+        }
+    } else {
+        for (int v = (int)L.nv - 1; v >= 0; v--) {
+            u64 q = rank / L.extent[v];
+            key |= (rank - q * L.extent[v]) << L.off[v];
+            rank = q;
+        }
+    }
+    return key;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers
+// ---------------------------------------------------------------------------
+
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+#define PM_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            throw ::pm::Error(e_ == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA,       \
+                              std::string(#call) + ": " + cudaGetErrorString(e_));         \
+    } while (0)
+
+#define PM_LAUNCHED(ctx)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess)                                                             \
+            throw ::pm::Error(PM_ECUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+        (ctx).launches++;                                                                  \
+    } while (0)
+
+// Stream-ordered scratch: every block comes from cudaMallocAsync on the call's
+// stream and goes back with cudaFreeAsync when the call ends.
+struct Scratch {
+    cudaStream_t s;
+    std::vector<void *> blocks;
+    explicit Scratch(cudaStream_t st) : s(st) {}
+    ~Scratch()
+    {
+        for (void *p : blocks) cudaFreeAsync(p, s);
+    }
+    template <class T>
+    T *get(size_t n)
+    {
+        void *p = nullptr;
+        size_t bytes = n * sizeof(T);
+        if (bytes < 256) bytes = 256;
+        cudaError_t e = cudaMallocAsync(&p, bytes, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(PM_ENOMEM, "cudaMallocAsync failed");
+        }
+        blocks.push_back(p);
+        return (T *)p;
+    }
+};
+
+struct Ctx {
+    cudaStream_t s;
+    u32 launches = 0;
+    u32 syncs = 0;
+    int sm_count = 148;
+    void sync()
+    {
+        PM_CUDA(cudaStreamSynchronize(s));
+        syncs++;
+    }
+};
+
+inline u32 ceil_div_u32(u64 a, u64 b) { return (u32)((a + b - 1) / b); }
+
+inline int bit_length(u64 x)
+{
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+// device primitives (pm_prims.cu)
+void scan_exclusive_u64(Ctx &c, Scratch &S, const u64 *in, u64 *out, size_t n);
+void radix_sort_pairs(Ctx &c, Scratch &S, u64 *keys, u64 *v0, u64 *v1, size_t n, int nbits);
+
+}  // namespace pm

@@ -1,0 +1,264 @@
+"""Parity of the CUDA path with the oracle, through the C-ABI.
+
+All coefficient arithmetic is exact, so the bar is bit-exact equality of keys
+and coefficients.  Small and medium cases are compared element by element
+with oracle.mul; the full-size workloads the benchmark times are checked on
+sampled outputs (oracle.coef_at, one monomial at a time), by evaluation at
+random points mod p (f(r) g(r) = h(r)) and by the closed-form term count.
+"""
+
+import math
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import polygen
+from tests.gpu_util import P61, assert_same, check_canonical, pack_np, run_gpu, unpack_np
+
+pytestmark = pytest.mark.gpu
+
+STRATS = [
+    dict(strategy="auto"),
+    dict(strategy="direct"),
+    dict(strategy="direct", slots=512),            # many ranges, ragged tails
+    dict(strategy="direct", slots=1000, ranges_per_sm=64),
+    dict(strategy="sort"),
+    dict(strategy="sort", chunk=256),              # single-monomial ranges above the chunk
+    dict(strategy="sort", chunk=1000),
+]
+
+
+def _oracle(w, fe=None, fc=None, ge=None, gc=None):
+    fe = w.f.exps if fe is None else fe
+    fc = w.f.coefs if fc is None else fc
+    ge = w.g.exps if ge is None else ge
+    gc = w.g.coefs if gc is None else gc
+    return oracle.mul(w.nvars, w.field_bits, w.kind, fe, fc, ge, gc)
+
+
+@pytest.mark.parametrize("opts", STRATS, ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
+def test_c1_exact(opts):
+    w = polygen.workload_c1()
+    ref = _oracle(w)
+    gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
+    check_canonical(gpu[0], gpu[1], w.field_bits)
+    assert_same(gpu, ref, w.field_bits)
+    assert gpu[2]["term_products"] == 10**6
+
+
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+@pytest.mark.parametrize("opts", STRATS[:5], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
+def test_dense_reduced_exact(kind, opts):
+    mons = polygen.monomials_total_degree(4, 10)          # 1001 monomials
+    st = polygen.Stream(1234, 0)
+    if kind == "m61":
+        fc, gc = st.coef_m61(len(mons)), st.coef_m61(len(mons))
+    else:
+        fc, gc = st.coef_i64(len(mons), 1 << 20), st.coef_i64(len(mons), 1 << 20)
+    ref = oracle.mul(4, [16] * 4, kind, mons, fc, mons[::-1], gc)
+    gpu = run_gpu([16] * 4, kind, mons, fc, mons[::-1], gc, **opts)
+    check_canonical(gpu[0], gpu[1], [16] * 4, kind)
+    assert_same(gpu, (ref[0], ref[1].reshape(-1)), [16] * 4)
+    assert len(ref[0]) == math.comb(4 + 20, 4)
+
+
+def _sampled_check(w, gpu, nsample=120, seed=0):
+    keys, coefs, _ = gpu
+    kind = w.kind
+    rnd = random.Random(seed)
+    n = keys.shape[0]
+    idx = sorted(rnd.sample(range(n), min(nsample, n)))
+    exps = unpack_np(keys[idx], w.field_bits)
+    want = oracle.coef_at(w.nvars, w.field_bits, kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, exps)
+    got = coefs.reshape(n, -1)[idx]
+    np.testing.assert_array_equal(got.reshape(want.shape), want)
+    # evaluation at random points: h(r) = f(r) g(r) mod p
+    for _ in range(2):
+        r = [rnd.randrange(P61) for _ in range(w.nvars)]
+        hk = "m61" if kind == "m61" else "i128"
+        hv = oracle.evaluate(w.nvars, hk, unpack_np(keys, w.field_bits), coefs.reshape(n, -1) if kind != "m61" else coefs, r)
+        fv = oracle.evaluate(w.nvars, kind, w.f.exps, w.f.coefs, r)
+        gv = oracle.evaluate(w.nvars, kind, w.g.exps, w.g.coefs, r)
+        assert hv == fv * gv % P61
+
+
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_c2_full_size(kind):
+    """The dense workload at full size: 10626 x 10626 terms, exactly
+    C(44, 4) = 135751 result terms, sampled coefficients, evaluation."""
+    w = polygen.workload_c2(kind)
+    gpu = run_gpu(w.field_bits, kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    check_canonical(gpu[0], gpu[1], w.field_bits, kind)
+    assert gpu[0].shape[0] == math.comb(44, 4)
+    assert gpu[2]["term_products"] == 10626 ** 2
+    _sampled_check(w, gpu)
+
+
+def test_c3_reduced_exact():
+    w = polygen.workload_c3(n=3000)
+    ref = _oracle(w)
+    for opts in (dict(strategy="auto"), dict(strategy="sort"), dict(strategy="direct", slots=4096)):
+        gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
+        assert_same(gpu, ref, w.field_bits)
+
+
+def test_c3_full_size():
+    """The sparse five-variable workload at full size (2.5e9 term products)."""
+    w = polygen.workload_c3()
+    gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    keys = gpu[0]
+    check_canonical(keys, gpu[1], w.field_bits)
+    assert keys.shape[0] <= 13 * 17 * 21 * 25 * 33
+    _sampled_check(w, gpu, nsample=60)
+    # monomials absent from the result have coefficient 0 in the oracle
+    rnd = random.Random(3)
+    box = [13, 17, 21, 25, 33]
+    cand = np.array([[rnd.randrange(b) for b in box] for _ in range(400)], dtype=np.uint32)
+    ck = pack_np(cand, w.field_bits)
+    pos = np.minimum(np.searchsorted(keys, ck), keys.shape[0] - 1)
+    absent = cand[keys[pos] != ck][:40]
+    assert absent.shape[0] > 0
+    z = oracle.coef_at(5, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, absent)
+    assert np.all(z == 0)
+
+
+@pytest.mark.parametrize("nv,nf,ng,seed", [(3, 16, 16, 1), (4, 700, 900, 2), (5, 100, 4096, 3),
+                                           (8, 4096, 350, 4), (6, 2500, 2500, 5), (3, 1, 4000, 6)])
+def test_sparse_exact(nv, nf, ng, seed):
+    w = polygen.sparse_product(polygen.Stream(seed, 0), nv, nf, ng)
+    ref = _oracle(w)
+    for opts in (dict(strategy="auto"), dict(strategy="sort", chunk=512)):
+        gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
+        check_canonical(gpu[0], gpu[1], w.field_bits)
+        assert_same(gpu, ref, w.field_bits)
+
+
+def test_sparse_heavy_collisions():
+    """Sparse supports with a small exponent cap: many products per monomial."""
+    w = polygen.sparse_product(polygen.Stream(77, 0), 4, 3000, 3000, exp_hi=7)
+    ref = _oracle(w)
+    for opts in (dict(strategy="auto"), dict(strategy="sort", chunk=300), dict(strategy="direct", slots=64)):
+        gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
+        assert_same(gpu, ref, w.field_bits)
+
+
+def test_commutative_bit_exact():
+    w = polygen.workload_c1()
+    a = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    b = run_gpu(w.field_bits, "m61", w.g.exps, w.g.coefs, w.f.exps, w.f.coefs)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+def test_power_closed_form():
+    """(1+x+y+z)^6 (1+x+y+z)^7 = (1+x+y+z)^13, multinomial coefficients."""
+    fe, fc = polygen.multinomial_power(3, 6)
+    ge, gc = polygen.multinomial_power(3, 7)
+    he, hc = polygen.multinomial_power(3, 13)
+    for s in ("direct", "sort"):
+        gpu = run_gpu([10] * 3, "m61", fe, np.array(fc, np.uint64), ge, np.array(gc, np.uint64), strategy=s)
+        order = np.lexsort(he.T[::-1])
+        np.testing.assert_array_equal(gpu[0], pack_np(he[order], [10] * 3))
+        np.testing.assert_array_equal(gpu[1], np.array(hc, np.uint64)[order])
+
+
+# ---------------------------------------------------------------------------
+# edge cases and error rules
+# ---------------------------------------------------------------------------
+
+def test_empty_and_zero_operands():
+    import paper_1303_7425_gb300 as P
+    e = np.zeros((0, 3), np.uint32)
+    c = np.zeros(0, np.uint64)
+    fe = np.array([[1, 2, 3], [0, 0, 1]], np.uint32)
+    k, co, st = run_gpu([8] * 3, "m61", fe, np.array([5, 7], np.uint64), e, c)
+    assert k.shape == (0,)
+    k, co, st = run_gpu([8] * 3, "m61", fe, np.array([0, P61], np.uint64), fe, np.array([1, 2], np.uint64))
+    assert k.shape == (0,)
+
+
+def test_duplicates_unsorted_and_unreduced_inputs():
+    rng = np.random.default_rng(5)
+    fe = rng.integers(0, 5, size=(400, 3)).astype(np.uint32)     # many repeats
+    ge = rng.integers(0, 5, size=(300, 3)).astype(np.uint32)
+    fc = rng.integers(0, 2**63, size=400, dtype=np.uint64) * np.uint64(2) + np.uint64(1)  # >= p too
+    gc = rng.integers(0, 2**63, size=300, dtype=np.uint64)
+    ref = oracle.mul(3, [8] * 3, "m61", fe, fc, ge, gc)
+    for s in ("direct", "sort"):
+        assert_same(run_gpu([8] * 3, "m61", fe, fc, ge, gc, strategy=s), ref, [8] * 3)
+
+
+@pytest.mark.parametrize("bits,hi", [([32, 32], (1 << 30) - 1), ([4] * 16, 3), ([1, 31, 32], 1 << 29),
+                                      ([20, 20, 20], (1 << 18) - 1)])
+def test_packing_extremes(bits, hi):
+    nv = len(bits)
+    st = polygen.Stream(11, nv)
+    lim = [min(hi, (1 << (b - 2)) - 1) if b >= 2 else 0 for b in bits]
+    fe = np.stack([st.below(l + 1, 300).astype(np.uint32) for l in lim], axis=1)
+    ge = np.stack([st.below(l + 1, 200).astype(np.uint32) for l in lim], axis=1)
+    fe[0] = lim
+    ge[0] = lim                                        # the largest exponent sum is reached
+    fc, gc = st.coef_m61(300), st.coef_m61(200)
+    ref = oracle.mul(nv, bits, "m61", fe, fc, ge, gc)
+    for s in ("auto", "sort"):
+        gpu = run_gpu(bits, "m61", fe, fc, ge, gc, strategy=s)
+        assert_same(gpu, ref, bits)
+
+
+def test_int128_near_bound():
+    a, b = -2**63, 2**63 - 1
+    fe = np.array([[0], [1]], np.uint32)
+    ref = oracle.mul(1, [8], "i64", fe, np.array([a, a], np.int64), fe, np.array([b, b], np.int64))
+    for s in ("direct", "sort"):
+        gpu = run_gpu([8], "i64", fe, np.array([a, a], np.int64), fe, np.array([b, b], np.int64), strategy=s)
+        assert_same(gpu, (ref[0], ref[1].reshape(-1)), [8])
+
+
+def _expect_error(code, *args, **kw):
+    import paper_1303_7425_gb300 as P
+    with pytest.raises(P.PolymulError) as ei:
+        run_gpu(*args, **kw)
+    assert ei.value.code == code
+    return ei.value
+
+
+def test_error_rules():
+    one = np.array([1], np.uint64)
+    _expect_error(-2, [4, 4], "m61", np.array([[8, 0]], np.uint32), one, np.array([[0, 0]], np.uint32), one)
+    _expect_error(-2, [4, 4], "m61", np.array([[4, 0]], np.uint32), one, np.array([[4, 0]], np.uint32), one)
+    fe = np.array([[0], [1]], np.uint32)
+    _expect_error(-3, [8], "i64", fe, np.array([-2**63, -2**63], np.int64), fe, np.array([-2**63, 1], np.int64))
+    _expect_error(-3, [8], "i64", np.array([[0], [0]], np.uint32), np.array([2**62, 2**62], np.int64),
+                  fe, np.array([1, 1], np.int64))
+    _expect_error(-1, [40, 30], "m61", fe.repeat(2, 1), np.array([1, 2], np.uint64), fe.repeat(2, 1),
+                  np.array([1, 2], np.uint64))
+
+
+def test_capacity_error_reports_needed_size():
+    import paper_1303_7425_gb300 as P
+    import torch
+    from tests.gpu_util import to_dev
+    w = polygen.workload_c1()
+    f = to_dev(w.f.exps, w.f.coefs)
+    g = to_dev(w.g.exps, w.g.coefs)
+    out = (torch.empty(10, dtype=torch.int64, device="cuda"), torch.empty(10, dtype=torch.int64, device="cuda"))
+    with pytest.raises(P.PolymulError) as ei:
+        P.polymul(w.field_bits, f[0], f[1], g[0], g[1], out=out)
+    assert ei.value.code == -4
+    ref = _oracle(w)
+    assert ei.value.needed == len(ref[0])
+
+
+def test_pack_unpack_roundtrip():
+    import paper_1303_7425_gb300 as P
+    import torch
+    bits = [7, 9, 11, 5]
+    st = polygen.Stream(3, 3)
+    e = np.stack([st.below(1 << (b - 1), 1000).astype(np.uint32) for b in bits], axis=1)
+    de = torch.from_numpy(e.view(np.int32)).cuda()
+    keys = P.pack(bits, de)
+    np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), pack_np(e, bits))
+    back = P.unpack(bits, keys)
+    np.testing.assert_array_equal(back.cpu().numpy().view(np.uint32), e)
