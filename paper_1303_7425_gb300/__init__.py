@@ -14,7 +14,8 @@ from ._native import (  # noqa: F401
     out_bound,
     pack,
     polymul,
+    probe_mac,
     unpack,
 )
 
-__all__ = ["polymul", "unpack", "pack", "out_bound", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["polymul", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

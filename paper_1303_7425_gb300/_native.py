@@ -62,7 +62,8 @@ class PolymulError(RuntimeError):
 
 
 # exported symbols, in include/polymul.h order
-SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_strerror", "pm_version")
+SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_strerror", "pm_version",
+           "pm_probe_mac")
 
 _lib = None
 
@@ -88,6 +89,8 @@ def lib():
         L.pm_strerror.restype = C.c_char_p
         L.pm_version.argtypes = []
         L.pm_version.restype = C.c_int
+        L.pm_probe_mac.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]
+        L.pm_probe_mac.restype = C.c_int
         _lib = L
     return _lib
 
@@ -216,3 +219,12 @@ def pack(field_bits: Sequence[int], exps, stream=None):
         if rc != PM_OK:
             raise PolymulError(rc, "pm_pack")
     return keys[:n]
+
+
+def probe_mac(blocks: int, threads: int, iters: int, sink, seed: int = 0x1303742500, stream=None) -> None:
+    """Launch the register-only multiply-accumulate probe (see
+    include/polymul_probe.h); time it with CUDA events on ``stream``."""
+    _check_cuda(sink)
+    rc = lib().pm_probe_mac(blocks, threads, iters, seed, sink.data_ptr(), _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_probe_mac")

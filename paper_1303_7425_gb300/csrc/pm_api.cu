@@ -7,37 +7,15 @@
 #include <cstring>
 #include <mutex>
 
+#include "pm_direct.cuh"
 #include "pm_pack.cuh"
 #include "pm_partition.cuh"
 #include "pm_range.cuh"
 
 namespace pm {
 
-constexpr u32 DEFAULT_SLOTS = 24576;   // direct: 192 KB of 64-bit accumulators
-constexpr u32 MAX_SLOTS = 24576;
 constexpr u32 DEFAULT_CHUNK = 4096;    // sort: term products per range
 constexpr u32 MAX_CHUNK = 4096;
-constexpr u32 DEFAULT_RANGES_PER_SM = 4;
-
-// K-e: copy each range's terms from its scratch slice to its final place
-__global__ void k_compact_copy(const u64 *__restrict__ skey, const u64 *__restrict__ scoef,
-                               const u64 *__restrict__ boff, const u64 *__restrict__ foff,
-                               const u64 *__restrict__ ucount, u32 nranges, u32 words, u64 *__restrict__ hkey,
-                               u64 *__restrict__ hcoef)
-{
-    for (u32 k = blockIdx.x; k < nranges; k += gridDim.x) {
-        const u64 src = boff[k], dst = foff[k], n = ucount[k];
-        for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
-            hkey[dst + t] = skey[src + t];
-            if (words == 1) {
-                hcoef[dst + t] = scoef[src + t];
-            } else {
-                hcoef[2 * (dst + t)] = scoef[2 * (src + t)];
-                hcoef[2 * (dst + t) + 1] = scoef[2 * (src + t) + 1];
-            }
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 
@@ -118,12 +96,40 @@ struct Small {  // host mirror of the small device block
     u32 maxe_f[PM_MAX_VARS], maxe_g[PM_MAX_VARS];
     u32 pad;
     u64 count_f, count_g, maxabs_f, maxabs_g;
+    u64 fl_f[2], fl_g[2];  // first and last canonical key of f and g
 };
 
 static void read_small(Ctx &c, Small &h, const Small *d)
 {
     PM_CUDA(cudaMemcpyAsync(&h, d, sizeof(Small), cudaMemcpyDeviceToHost, c.s));
     c.sync();
+}
+
+static u64 host_rank(const Layout &L, u64 key)
+{
+    u64 r = 0;
+    for (u32 v = 0; v < L.nv; v++) r += ((key >> L.off[v]) & ((1ull << L.width[v]) - 1)) * L.stride[v];
+    return r;
+}
+
+// K-e for groups/ranges whose scratch slice starts at base[k] - base0
+__global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__restrict__ scoef,
+                                 const u64 *__restrict__ base, u64 base0, const u64 *__restrict__ foff,
+                                 const u64 *__restrict__ ucount, u32 nslices, u32 words, u64 *__restrict__ hkey,
+                                 u64 *__restrict__ hcoef)
+{
+    for (u32 k = blockIdx.x; k < nslices; k += gridDim.x) {
+        const u64 src = base[k] - base0, dst = foff[k], n = ucount[k];
+        for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
+            hkey[dst + t] = skey[src + t];
+            if (words == 1) {
+                hcoef[dst + t] = scoef[src + t];
+            } else {
+                hcoef[2 * (dst + t)] = scoef[2 * (src + t)];
+                hcoef[2 * (dst + t) + 1] = scoef[2 * (src + t) + 1];
+            }
+        }
+    }
 }
 
 static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, const pm_terms_in *g,
@@ -139,8 +145,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.slots > MAX_SLOTS || o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2)
-        throw Error(PM_EINVAL, "bad options");
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2) throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
     memset(&stats, 0, sizeof(stats));
 
@@ -151,15 +156,9 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     Small hs;
     Small *ds = S.get<Small>(1);
     PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
-
-    // K-a (1): input guard bits and the raw exponent box
-    Layout L = base_layout(*pk);
-    input_maxima(c, *f, L, ds->maxe_f, &ds->status);
-    input_maxima(c, *g, L, ds->maxe_g, &ds->status);
-    read_small(c, hs, ds);
-    if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
-    auto finish_empty = [&]() {
-        h->n = 0;
+    auto finish = [&](u64 n_out) {
+        h->n = n_out;
+        stats.n_out = n_out;
         if (st) {
             stats.kernel_launches = c.launches;
             stats.host_syncs = c.syncs;
@@ -167,27 +166,31 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         }
         return PM_OK;
     };
-    if (f->n == 0 || g->n == 0) return finish_empty();
+
+    // K-a (1): input guard bits and the raw exponent box            [sync 1]
+    Layout L = base_layout(*pk);
+    input_maxima(c, *f, L, ds->maxe_f, &ds->status);
+    input_maxima(c, *g, L, ds->maxe_g, &ds->status);
+    read_small(c, hs, ds);
+    if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
+    if (f->n == 0 || g->n == 0) return finish(0);
     Layout raw = L;
     const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
 
-    // K-a (2): canonical operands
+    // K-a (2): canonical operands, their maxima, extremes and sizes    [sync 2]
     Operand F, G;
     canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
     canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
     PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * 2 * PM_MAX_VARS, c.s));
+    operand_stats(c, F, f->n, &ds->count_f, L, kind, ds->maxe_f, &ds->maxabs_f, ds->fl_f);
+    operand_stats(c, G, g->n, &ds->count_g, L, kind, ds->maxe_g, &ds->maxabs_g, ds->fl_g);
     read_small(c, hs, ds);
     if (hs.status & ST_COEF_BOUND) throw Error(PM_ECOEF_BOUND, "repeated input monomial leaves int64");
     F.n = hs.count_f;
     G.n = hs.count_g;
     stats.n_f = F.n;
     stats.n_g = G.n;
-    if (F.n == 0 || G.n == 0) return finish_empty();
-
-    // K-a (3): exponent-sum guard, int128 bound, the product's box
-    operand_stats(c, F, L, kind, ds->maxe_f, &ds->maxabs_f);
-    operand_stats(c, G, L, kind, ds->maxe_g, &ds->maxabs_g);
-    read_small(c, hs, ds);
+    if (F.n == 0 || G.n == 0) return finish(0);
     for (u32 v = 0; v < L.nv; v++)
         if ((u64)hs.maxe_f[v] + hs.maxe_g[v] >= (1ull << (L.width[v] - 1)))
             throw Error(PM_EEXP_OVERFLOW, "product exponent reaches its guard bit");
@@ -200,38 +203,78 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     const u64 products = F.n * G.n;
     stats.term_products = products;
     stats.box = box;
+    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
 
-    // strategy (autotuner defaults; see pm_tune)
+    // strategy choice (autotuner defaults)
     int strategy = o.strategy;
-    const u32 slots_max = kind == PM_COEF_M61 ? MAX_SLOTS : MAX_SLOTS / 2;
-    u32 slots = o.slots ? o.slots : DEFAULT_SLOTS;
-    if (slots > slots_max) slots = slots_max;
+    const u32 slots_max = direct_max_slots(kind);
+    u32 slots = o.slots ? o.slots : slots_max;
+    if (slots > slots_max) throw Error(PM_EINVAL, "slots exceed shared memory");
     const u32 chunk = o.chunk ? o.chunk : DEFAULT_CHUNK;
-    const u32 rps = o.ranges_per_sm ? o.ranges_per_sm : DEFAULT_RANGES_PER_SM;
     if (strategy == PM_STRATEGY_AUTO) {
-        bool dense = box <= 16 * products && box / slots < (1ull << 22);
-        strategy = dense ? PM_STRATEGY_DIRECT : PM_STRATEGY_SORT;
+        // direct addressing pays when the rank box is not much larger than
+        // the work: every slot of the box is cleared and scanned once
+        strategy = box <= 16 * products && box < (1ull << 40) ? PM_STRATEGY_DIRECT : PM_STRATEGY_SORT;
     }
-    if (strategy == PM_STRATEGY_DIRECT && box / slots >= (1ull << 23))
+    if (strategy == PM_STRATEGY_DIRECT && box >= (1ull << 40))
         throw Error(PM_EINVAL, "exponent box too large for the direct strategy");
     stats.strategy = strategy;
 
-    // K-b: output ranges
-    PartitionPlan plan;
-    const u64 *A, *B;
+    u64 *okey, *ocoef, *ucount, *foff, *slice_base;
+    u64 slice_base0;
+    u32 nslices;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (st) {
+        PM_CUDA(cudaEventCreate(&e0));
+        PM_CUDA(cudaEventCreate(&e1));
+    }
+
     if (strategy == PM_STRATEGY_DIRECT) {
+        // K-b: ranks, grid sample, groups (no host sync)
+        u32 *g32 = S.get<u32>(G.n);
         operand_ranks(c, F, L);
-        operand_ranks(c, G, L);
-        A = F.rank;
-        B = G.rank;
-        plan.uniform_step = slots;
-        u64 tgt = products / ((u64)rps * c.sm_count);
-        plan.target = tgt < 32768 ? 32768 : tgt;
-        plan.hard_target = false;
-        plan.max_rounds = 4;
+        operand_ranks(c, G, L, g32);
+        const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
+        const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        const u32 gps = o.ranges_per_sm ? o.ranges_per_sm : 2;
+        u64 G64 = (u64)gps * c.sm_count;
+        if (G64 > end - lo) G64 = end - lo;
+        // per-group edge scratch: 8 bytes per row of f
+        while (G64 > 1 && G64 * 8 * F.n > (4ull << 30)) G64 /= 2;
+        const u32 Gn = (u32)G64;
+        u32 l = 1;
+        while ((u64)(l + 1) * (l + 1) < 32ull * Gn && l < 4096) l++;
+        const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l);
+        okey = S.get<u64>(end - lo);
+        ocoef = S.get<u64>((end - lo) * words);
+        ucount = S.get<u64>(Gn + 1);
+        DirectArgs a;
+        memset(&a, 0, sizeof(a));
+        a.A = F.rank;
+        a.Ac = F.coef;
+        a.B = G.rank;
+        a.Bc = G.coef;
+        a.B32 = g32;
+        a.na = (u32)F.n;
+        a.nb = (u32)G.n;
+        a.gb = gb;
+        a.ngroups = Gn;
+        a.lo = lo;
+        a.edges = S.get<u32>((size_t)Gn * 2 * F.n);
+        a.okey = okey;
+        a.ocoef = ocoef;
+        a.ucount = ucount;
+        a.L = L;
+        if (st) PM_CUDA(cudaEventRecord(e0, c.s));
+        launch_direct(c, a, slots, kind);
+        if (st) PM_CUDA(cudaEventRecord(e1, c.s));
+        stats.n_ranges = Gn;
+        slice_base = const_cast<u64 *>(gb);
+        slice_base0 = lo;
+        nslices = Gn;
     } else {
-        A = F.key;
-        B = G.key;
+        // K-b: grid splitters, counts, refinement to the chunk capacity
+        PartitionPlan plan;
         double want = 4.0 * (double)products / chunk;
         u32 l = 1;
         while ((double)(l + 1) * (l + 1) < want && l < 2048) l++;
@@ -239,48 +282,43 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         plan.target = chunk;
         plan.hard_target = true;
         plan.max_rounds = 64;
+        Ranges R = partition(c, S, F.key, (u32)F.n, G.key, (u32)G.n, plan);
+        stats.n_ranges = R.n;
+        stats.refine_rounds = R.rounds;
+        RangeArgs a;
+        memset(&a, 0, sizeof(a));
+        a.fkey = F.key;
+        a.fcoef = F.coef;
+        a.gkey = G.key;
+        a.gcoef = G.coef;
+        a.na = (u32)F.n;
+        a.nb = (u32)G.n;
+        a.rlo = R.lo;
+        a.rhi = R.hi;
+        a.rO = R.O;
+        a.boff = R.boff;
+        a.nranges = R.n;
+        okey = S.get<u64>(R.out_bound + 1);
+        ocoef = S.get<u64>((R.out_bound + 1) * words);
+        ucount = S.get<u64>(R.n + 1);
+        a.okey = okey;
+        a.ocoef = ocoef;
+        a.ucount = ucount;
+        a.L = L;
+        a.status = &ds->status;
+        if (st) PM_CUDA(cudaEventRecord(e0, c.s));
+        if (R.n) launch_range_sort(c, a, chunk, kind, R.n);
+        if (st) PM_CUDA(cudaEventRecord(e1, c.s));
+        slice_base = R.boff;
+        slice_base0 = 0;
+        nslices = R.n;
     }
-    Ranges R = partition(c, S, A, (u32)F.n, B, (u32)G.n, plan);
-    stats.n_ranges = R.n;
-    stats.refine_rounds = R.rounds;
 
-    // K-c/K-d: one CTA per range
-    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
-    RangeArgs a;
-    memset(&a, 0, sizeof(a));
-    a.fkey = A;
-    a.fcoef = F.coef;
-    a.gkey = B;
-    a.gcoef = G.coef;
-    a.na = (u32)F.n;
-    a.nb = (u32)G.n;
-    a.rlo = R.lo;
-    a.rhi = R.hi;
-    a.rO = R.O;
-    a.boff = R.boff;
-    a.nranges = R.n;
-    a.okey = S.get<u64>(R.out_bound + 1);
-    a.ocoef = S.get<u64>((R.out_bound + 1) * words);
-    a.ucount = S.get<u64>(R.n + 1);
-    a.L = L;
-    a.status = &ds->status;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (st) {
-        PM_CUDA(cudaEventCreate(&e0));
-        PM_CUDA(cudaEventCreate(&e1));
-        PM_CUDA(cudaEventRecord(e0, c.s));
-    }
-    if (R.n) {
-        if (strategy == PM_STRATEGY_DIRECT) launch_range_direct(c, a, slots, kind, R.n);
-        else launch_range_sort(c, a, chunk, kind, R.n);
-    }
-    if (st) PM_CUDA(cudaEventRecord(e1, c.s));
-
-    // K-e: concatenate the ranges in ascending order
-    u64 *foff = S.get<u64>(R.n + 1);
-    scan_exclusive_u64(c, S, a.ucount, foff, R.n);
+    // K-e: concatenate the slices in ascending order                  [sync 3]
+    foff = S.get<u64>(nslices + 1);
+    scan_exclusive_u64(c, S, ucount, foff, nslices);
     u64 n_out = 0;
-    PM_CUDA(cudaMemcpyAsync(&n_out, foff + R.n, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
+    PM_CUDA(cudaMemcpyAsync(&n_out, foff + nslices, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
     PM_CUDA(cudaMemcpyAsync(&hs.status, &ds->status, sizeof(u32), cudaMemcpyDeviceToHost, c.s));
     c.sync();
     if (st) {
@@ -292,22 +330,20 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     stats.n_out = n_out;
     if (n_out > h->cap) {
         h->n = n_out;
-        if (st) *st = stats;
+        if (st) {
+            stats.kernel_launches = c.launches;
+            stats.host_syncs = c.syncs;
+            *st = stats;
+        }
         return PM_ECAPACITY;
     }
-    if (R.n && n_out) {
-        unsigned grid = R.n < 65535u ? R.n : 65535u;
-        k_compact_copy<<<grid, 256, 0, c.s>>>(a.okey, a.ocoef, R.boff, foff, a.ucount, R.n, words, (u64 *)h->keys,
-                                              (u64 *)h->coefs);
+    if (nslices && n_out) {
+        unsigned grid = nslices < 65535u ? nslices : 65535u;
+        k_compact_slices<<<grid, 256, 0, c.s>>>(okey, ocoef, slice_base, slice_base0, foff, ucount, nslices, words,
+                                                (u64 *)h->keys, (u64 *)h->coefs);
         PM_LAUNCHED(c);
     }
-    h->n = n_out;
-    if (st) {
-        stats.kernel_launches = c.launches;
-        stats.host_syncs = c.syncs;
-        *st = stats;
-    }
-    return PM_OK;
+    return finish(n_out);
 }
 
 }  // namespace pm

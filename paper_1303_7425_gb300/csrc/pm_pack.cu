@@ -87,14 +87,21 @@ __global__ void k_combine_scatter(const u64 *__restrict__ key, const u64 *__rest
     ocoef[pos[i]] = val[i];
 }
 
-// per-field maxima of canonical keys and max |coef| (int64 kind)
-__global__ void k_operand_stats(const u64 *__restrict__ key, const u64 *__restrict__ coef, size_t n, Layout L,
-                                int kind, u32 *__restrict__ maxe, u64 *__restrict__ maxabs)
+// per-field maxima of canonical keys, max |coef| (int64 kind), and the
+// first and last key; the operand size is read from the device
+__global__ void k_operand_stats(const u64 *__restrict__ key, const u64 *__restrict__ coef,
+                                const u64 *__restrict__ d_n, Layout L, int kind, u32 *__restrict__ maxe,
+                                u64 *__restrict__ maxabs, u64 *__restrict__ first_last)
 {
     __shared__ u32 m[PM_MAX_VARS];
     __shared__ u64 ma;
+    const size_t n = *d_n;
     if (threadIdx.x < PM_MAX_VARS) m[threadIdx.x] = 0;
     if (threadIdx.x == 0) ma = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && n) {
+        first_last[0] = key[0];
+        first_last[1] = key[n - 1];
+    }
     __syncthreads();
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         u64 k = key[i];
@@ -110,10 +117,15 @@ __global__ void k_operand_stats(const u64 *__restrict__ key, const u64 *__restri
     if (threadIdx.x == 0 && kind != PM_COEF_M61) atomicMax(maxabs, ma);
 }
 
-__global__ void k_ranks(const u64 *__restrict__ key, size_t n, Layout L, u64 *__restrict__ rank)
+__global__ void k_ranks(const u64 *__restrict__ key, size_t n, Layout L, u64 *__restrict__ rank,
+                        u32 *__restrict__ rank32)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) rank[i] = key_to_rank(L, key[i]);
+    if (i < n) {
+        const u64 r = key_to_rank(L, key[i]);
+        rank[i] = r;
+        if (rank32) rank32[i] = (u32)r;
+    }
 }
 
 __global__ void k_pack_only(const u32 *__restrict__ exps, size_t n, Layout L, u64 *__restrict__ key,
@@ -182,19 +194,20 @@ void canonicalize(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &raw, 
     PM_CUDA(cudaMemcpyAsync(d_count, pos + n, sizeof(u64), cudaMemcpyDeviceToDevice, c.s));
 }
 
-void operand_stats(Ctx &c, const Operand &op, const Layout &L, int kind, u32 *d_maxe, u64 *d_maxabs)
+void operand_stats(Ctx &c, const Operand &op, u64 n_max, const u64 *d_n, const Layout &L, int kind, u32 *d_maxe,
+                   u64 *d_maxabs, u64 *d_first_last)
 {
-    if (op.n == 0) return;
-    unsigned g = grid_for(op.n, 256);
+    if (n_max == 0) return;
+    unsigned g = grid_for(n_max, 256);
     if (g > (unsigned)(c.sm_count * 4)) g = c.sm_count * 4;
-    k_operand_stats<<<g, 256, 0, c.s>>>(op.key, op.coef, op.n, L, kind, d_maxe, d_maxabs);
+    k_operand_stats<<<g, 256, 0, c.s>>>(op.key, op.coef, d_n, L, kind, d_maxe, d_maxabs, d_first_last);
     PM_LAUNCHED(c);
 }
 
-void operand_ranks(Ctx &c, Operand &op, const Layout &L)
+void operand_ranks(Ctx &c, Operand &op, const Layout &L, u32 *rank32)
 {
     if (op.n == 0) return;
-    k_ranks<<<grid_for(op.n, 256), 256, 0, c.s>>>(op.key, op.n, L, op.rank);
+    k_ranks<<<grid_for(op.n, 256), 256, 0, c.s>>>(op.key, op.n, L, op.rank, rank32);
     PM_LAUNCHED(c);
 }
 

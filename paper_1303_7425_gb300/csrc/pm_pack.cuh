@@ -19,8 +19,10 @@ struct Operand {
 void input_maxima(Ctx &c, const pm_terms_in &in, const Layout &L, u32 *d_maxe, u32 *d_status);
 void canonicalize(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &raw, u64 raw_box, int kind,
                   Operand &op, u32 *d_status, u64 *d_count);
-void operand_stats(Ctx &c, const Operand &op, const Layout &L, int kind, u32 *d_maxe, u64 *d_maxabs);
-void operand_ranks(Ctx &c, Operand &op, const Layout &L);
+void operand_stats(Ctx &c, const Operand &op, u64 n_max, const u64 *d_n, const Layout &L, int kind, u32 *d_maxe,
+                   u64 *d_maxabs, u64 *d_first_last);
+// rank32 (optional): also store the low 32 bits of each rank
+void operand_ranks(Ctx &c, Operand &op, const Layout &L, u32 *rank32 = nullptr);
 void pack_keys(Ctx &c, const u32 *exps, size_t n, const Layout &L, u64 *keys, u32 *d_status);
 void unpack_keys(Ctx &c, const u64 *keys, size_t n, const Layout &L, u32 *exps);
 

@@ -143,6 +143,13 @@ __global__ void k_ranges_emit(const u64 *__restrict__ Sp, const u64 *__restrict_
 
 static unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t ? (n + t - 1) / t : 1); }
 
+void grid_sample(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, u32 si, u32 sj, u32 stagger, u32 R, u32 Cc,
+                 u64 total, u64 *out)
+{
+    k_grid<<<blocks_for(total, 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, total, out);
+    PM_LAUNCHED(c);
+}
+
 static void count_at(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, const u64 *Sp, u32 ns, u64 *cnt)
 {
     unsigned g = ns < (u32)(c.sm_count * 16) ? ns : (unsigned)(c.sm_count * 16);
@@ -187,8 +194,7 @@ Ranges partition(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb,
         u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
         u64 total = (u64)R * Cc + Cc + R;
         u64 *cand = S.get<u64>(total + 1);
-        k_grid<<<blocks_for(total, 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, total, cand);
-        PM_LAUNCHED(c);
+        grid_sample(c, A, na, B, nb, si, sj, stagger, R, Cc, total, cand);
         k_set_u64<<<1, 1, 0, c.s>>>(cand + total, end);  // gamma_end
         PM_LAUNCHED(c);
         total += 1;

@@ -25,6 +25,11 @@ struct Ranges {
     u32 rounds = 0;
 };
 
+// the Sec. 5 grid points A[i] + B[j] (steps si, sj, alternate rows shifted by
+// `stagger`, plus the last row and column): `total` values into out
+void grid_sample(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, u32 si, u32 sj, u32 stagger, u32 R, u32 Cc,
+                 u64 total, u64 *out);
+
 Ranges partition(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, const PartitionPlan &plan);
 
 }  // namespace pm

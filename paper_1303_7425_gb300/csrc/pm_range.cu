@@ -7,12 +7,9 @@
 // (2) forms the range's term products, staging per-row data in shared memory
 //     and reading the other operand's coefficients with coalesced loads,
 // (3) accumulates them in shared memory -- the "MergeSort" of Alg. 1 -- with
-//     one of two strategies:
-//       direct: a slot per monomial rank in [lo, hi) (ranks are the
-//               mixed-radix index of the exponent vector in the product's
-//               exponent box; rank(alpha) + rank(beta) = rank(alpha + beta));
-//       sort:   an LSD radix sort of the range's (key, product) pairs on the
-//               bits that vary inside [lo, hi), then a segmented reduction,
+//     an LSD radix sort of the range's (key, product) pairs on the bits
+//     that vary inside [lo, hi), then a segmented reduction (the
+//     direct-addressed strategy lives in pm_direct.cu),
 // (4) writes its non-zero terms in ascending order to the range's slice of
 //     the output scratch (concatenation happens in K-e).
 #include "pm_range.cuh"
@@ -109,84 +106,6 @@ __device__ __forceinline__ void for_each_product(const RowTables &t, u32 nrows, 
         while (t.off[r + 1] <= p) r++;
         u32 j = t.jlo[r] + (p - t.off[r]);
         fn(r, j, p);
-    }
-}
-
-// ---------------------------------------------------------------------------
-// direct-addressed accumulation
-// ---------------------------------------------------------------------------
-
-template <int KIND>
-__global__ void __launch_bounds__(RK_THREADS) k_range_direct(RangeArgs a, u32 slots)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ u64 ws[32];
-    __shared__ u32 win[2];
-    const u32 words = KIND == PM_COEF_M61 ? 1 : 2;
-    u64 *acc = (u64 *)smem;  // M61: slots words; I64: lo[slots], hi[slots]
-    RowTables t = carve_rows(smem + (size_t)slots * 8 * words);
-    const u32 tid = threadIdx.x;
-
-    for (u32 k = blockIdx.x; k < a.nranges; k += gridDim.x) {
-        const u64 lo = a.rlo[k], hi = a.rhi[k];
-        const u32 span = (u32)(hi - lo);
-        for (u32 s = tid; s < span; s += RK_THREADS) {
-            acc[s] = 0;
-            if (KIND != PM_COEF_M61) acc[slots + s] = 0;
-        }
-        if (tid == 0) row_window(a, lo, hi, win[0], win[1]);
-        __syncthreads();
-        const u32 i0 = win[0], i1 = win[1];
-        for (u32 base = i0; base < i1; base += ROWS) {
-            u32 nrows;
-            u32 total = stage_rows(a, t, base, i1, lo, hi, ws, nrows);
-            for_each_product(t, nrows, total, [&](u32 r, u32 j, u32) {
-                const u64 gk = __ldg(a.gkey + j);
-                const u32 slot = (u32)(t.rkey[r] + gk - lo);
-                if (KIND == PM_COEF_M61) {
-                    m61_atomic_accumulate(&acc[slot], m61_mul_lazy(t.rcoef[r], __ldg(a.gcoef + j)));
-                } else {
-                    u64 plo, phi;
-                    mul_i64_wide((i64)t.rcoef[r], (i64)__ldg(a.gcoef + j), plo, phi);
-                    u64 old = atomicAdd(&acc[slot], plo);
-                    atomicAdd(&acc[slots + slot], phi + (old + plo < old ? 1ull : 0ull));
-                }
-            });
-            __syncthreads();
-        }
-        // emit non-zero slots in ascending rank order
-        const u64 obase = a.boff[k];
-        u64 run = 0;
-        for (u32 c0 = 0; c0 < span; c0 += RK_THREADS) {
-            const u32 s = c0 + tid;
-            u64 v0 = 0, v1 = 0;
-            bool nz = false;
-            if (s < span) {
-                if (KIND == PM_COEF_M61) {
-                    v0 = m61_reduce(acc[s]);
-                    nz = v0 != 0;
-                } else {
-                    v0 = acc[s];
-                    v1 = acc[slots + s];
-                    nz = (v0 | v1) != 0;
-                }
-            }
-            u64 cnt;
-            u64 pos = block_exclusive_scan(nz ? 1 : 0, cnt, ws);
-            if (nz) {
-                const u64 d = obase + run + pos;
-                a.okey[d] = rank_to_key(a.L, lo + s);
-                if (KIND == PM_COEF_M61) {
-                    a.ocoef[d] = v0;
-                } else {
-                    a.ocoef[2 * d] = v0;
-                    a.ocoef[2 * d + 1] = v1;
-                }
-            }
-            run += cnt;
-        }
-        if (tid == 0) a.ucount[k] = run;
-        __syncthreads();
     }
 }
 
@@ -423,11 +342,6 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
 // host launchers
 // ---------------------------------------------------------------------------
 
-size_t direct_smem_bytes(u32 slots, int kind)
-{
-    return (size_t)slots * 8 * (kind == PM_COEF_M61 ? 1 : 2) + ROW_TABLE_BYTES;
-}
-
 size_t sort_smem_bytes(u32 chunk, int kind)
 {
     size_t sort_bytes = (size_t)chunk * 8 * (kind == PM_COEF_M61 ? 3 : 4) + RK_WARPS * 256 * 4 + (size_t)chunk * 4;
@@ -438,19 +352,6 @@ template <class K>
 static void set_smem(K kernel, size_t bytes)
 {
     PM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
-
-void launch_range_direct(Ctx &c, const RangeArgs &a, u32 slots, int kind, unsigned grid)
-{
-    size_t bytes = direct_smem_bytes(slots, kind);
-    if (kind == PM_COEF_M61) {
-        set_smem(k_range_direct<PM_COEF_M61>, bytes);
-        k_range_direct<PM_COEF_M61><<<grid, RK_THREADS, bytes, c.s>>>(a, slots);
-    } else {
-        set_smem(k_range_direct<PM_COEF_I64_ACC128>, bytes);
-        k_range_direct<PM_COEF_I64_ACC128><<<grid, RK_THREADS, bytes, c.s>>>(a, slots);
-    }
-    PM_LAUNCHED(c);
 }
 
 void launch_range_sort(Ctx &c, const RangeArgs &a, u32 chunk, int kind, unsigned grid)

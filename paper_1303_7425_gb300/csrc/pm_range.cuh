@@ -17,9 +17,7 @@ struct RangeArgs {
     u32 *status;
 };
 
-size_t direct_smem_bytes(u32 slots, int kind);
 size_t sort_smem_bytes(u32 chunk, int kind);
-void launch_range_direct(Ctx &c, const RangeArgs &a, u32 slots, int kind, unsigned grid);
 void launch_range_sort(Ctx &c, const RangeArgs &a, u32 chunk, int kind, unsigned grid);
 
 }  // namespace pm
