@@ -93,11 +93,18 @@ typedef struct pm_terms_out {
 #define PM_STRATEGY_SORT   2  /* shared-memory radix sort + segmented reduce       */
 
 /* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
+/* Direct strategy accumulators (mod p kind). */
+#define PM_ACC_AUTO   0  /* limbs when min(n_f, n_g) <= 65537, else wide        */
+#define PM_ACC_WIDE   1  /* 64-bit sum + 32-bit wrap count per slot             */
+#define PM_ACC_LIMBS  2  /* four 16-bit limbs in 32-bit counters per slot       */
+
 typedef struct pm_options {
-    int32_t strategy;          /* PM_STRATEGY_*                                   */
-    uint32_t slots;            /* direct: output slots per range (<= 24576)        */
-    uint32_t chunk;            /* sort: term products per range (<= 4096)          */
-    uint32_t ranges_per_sm;    /* load-balance target: ranges per SM               */
+    int32_t strategy;          /* PM_STRATEGY_*                                     */
+    uint32_t slots;            /* direct: output slots per window (0 = the most
+                                  shared memory allows)                            */
+    uint32_t chunk;            /* sort: term products per range (<= 4096)            */
+    uint32_t ranges_per_sm;    /* direct: groups per SM; sort: unused                 */
+    int32_t accumulator;       /* PM_ACC_*; PM_ACC_LIMBS needs min(n_f, n_g) <= 65537 */
 } pm_options;
 
 /* Per-call counters (all optional; pass NULL). */

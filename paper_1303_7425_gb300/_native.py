@@ -22,6 +22,7 @@ PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA = -4, -5, -6, -7
 KIND = {"m61": 0, "i64": 1}
 STRATEGY = {"auto": 0, "direct": 1, "sort": 2}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
+ACCUMULATOR = {"auto": 0, "wide": 1, "limbs": 2}
 
 
 class pm_packing(C.Structure):
@@ -38,7 +39,7 @@ class pm_terms_out(C.Structure):
 
 class pm_options(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("slots", C.c_uint32), ("chunk", C.c_uint32),
-                ("ranges_per_sm", C.c_uint32)]
+                ("ranges_per_sm", C.c_uint32), ("accumulator", C.c_int32)]
 
 
 class pm_stats(C.Structure):
@@ -103,12 +104,14 @@ def packing(field_bits: Sequence[int]) -> pm_packing:
     return pk
 
 
-def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0) -> pm_options:
+def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
+            accumulator: str = "auto") -> pm_options:
     o = pm_options()
     o.strategy = STRATEGY[strategy]
     o.slots = slots
     o.chunk = chunk
     o.ranges_per_sm = ranges_per_sm
+    o.accumulator = ACCUMULATOR[accumulator]
     return o
 
 
@@ -157,7 +160,7 @@ def out_bound(field_bits, f_exps, g_exps, stream=None) -> int:
 
 def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61",
             strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
-            out=None, stream=None) -> Product:
+            accumulator: str = "auto", out=None, stream=None) -> Product:
     """h = f * g on the current CUDA device.
 
     f_exps/g_exps: (n, nvars) int32/uint32 CUDA tensors; f_coefs/g_coefs: (n,)
@@ -183,7 +186,7 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
     h.coefs = coefs.data_ptr()
     h.cap = cap
     st = pm_stats()
-    o = options(strategy, slots, chunk, ranges_per_sm)
+    o = options(strategy, slots, chunk, ranges_per_sm, accumulator)
     rc = lib().pm_polymul(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(o),
                           C.byref(st), _stream_handle(stream))
     if rc != PM_OK:

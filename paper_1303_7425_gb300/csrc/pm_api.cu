@@ -145,7 +145,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2) throw Error(PM_EINVAL, "bad options");
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2 || o.accumulator < 0 || o.accumulator > 2)
+        throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
     memset(&stats, 0, sizeof(stats));
 
@@ -179,8 +180,19 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
 
     // K-a (2): canonical operands, their maxima, extremes and sizes    [sync 2]
     Operand F, G;
-    canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
-    canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
+    {
+        // an operand whose own exponent box is small is canonicalised by a
+        // scatter into that box, otherwise by a radix sort on its ranks
+        const u32 zero[PM_MAX_VARS] = {0};
+        Layout own_f = L, own_g = L;
+        const u64 box_f = set_box(own_f, hs.maxe_f, zero);
+        const u64 box_g = set_box(own_g, hs.maxe_g, zero);
+        auto dense_ok = [](u64 box, u64 n) { return box <= (1ull << 26) && box <= 16 * n + 65536; };
+        if (dense_ok(box_f, f->n)) canonicalize_dense(c, S, *f, own_f, box_f, kind, F, &ds->status, &ds->count_f);
+        else canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
+        if (dense_ok(box_g, g->n)) canonicalize_dense(c, S, *g, own_g, box_g, kind, G, &ds->status, &ds->count_g);
+        else canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
+    }
     PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * 2 * PM_MAX_VARS, c.s));
     operand_stats(c, F, f->n, &ds->count_f, L, kind, ds->maxe_f, &ds->maxabs_f, ds->fl_f);
     operand_stats(c, G, g->n, &ds->count_g, L, kind, ds->maxe_g, &ds->maxabs_g, ds->fl_g);
@@ -207,7 +219,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
 
     // strategy choice (autotuner defaults)
     int strategy = o.strategy;
-    const u32 slots_max = direct_max_slots(kind);
+    const u32 slots_max = direct_max_slots(kind, F.n < G.n ? F.n : G.n, o.accumulator);
     u32 slots = o.slots ? o.slots : slots_max;
     if (slots > slots_max) throw Error(PM_EINVAL, "slots exceed shared memory");
     const u32 chunk = o.chunk ? o.chunk : DEFAULT_CHUNK;
@@ -232,19 +244,18 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (strategy == PM_STRATEGY_DIRECT) {
         // K-b: ranks, grid sample, groups (no host sync)
         u32 *g32 = S.get<u32>(G.n);
-        operand_ranks(c, F, L);
+        u32 *f32 = box <= 0xFFFFFFFFull ? S.get<u32>(F.n) : nullptr;
+        operand_ranks(c, F, L, f32);
         operand_ranks(c, G, L, g32);
         const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
         const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
-        const u32 gps = o.ranges_per_sm ? o.ranges_per_sm : 2;
+        const u32 gps = o.ranges_per_sm ? o.ranges_per_sm : 1;
         u64 G64 = (u64)gps * c.sm_count;
         if (G64 > end - lo) G64 = end - lo;
-        // per-group edge scratch: 8 bytes per row of f
-        while (G64 > 1 && G64 * 8 * F.n > (4ull << 30)) G64 /= 2;
         const u32 Gn = (u32)G64;
         u32 l = 1;
-        while ((u64)(l + 1) * (l + 1) < 32ull * Gn && l < 4096) l++;
-        const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l);
+        while ((u64)(l + 1) * (l + 1) < 256ull * Gn && l < 4096) l++;
+        const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, 1.0);
         okey = S.get<u64>(end - lo);
         ocoef = S.get<u64>((end - lo) * words);
         ucount = S.get<u64>(Gn + 1);
@@ -255,18 +266,18 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         a.B = G.rank;
         a.Bc = G.coef;
         a.B32 = g32;
+        a.A32 = f32;
         a.na = (u32)F.n;
         a.nb = (u32)G.n;
         a.gb = gb;
         a.ngroups = Gn;
         a.lo = lo;
-        a.edges = S.get<u32>((size_t)Gn * 2 * F.n);
         a.okey = okey;
         a.ocoef = ocoef;
         a.ucount = ucount;
         a.L = L;
         if (st) PM_CUDA(cudaEventRecord(e0, c.s));
-        launch_direct(c, a, slots, kind);
+        launch_direct(c, S, a, slots, kind, o.accumulator, end);
         if (st) PM_CUDA(cudaEventRecord(e1, c.s));
         stats.n_ranges = Gn;
         slice_base = const_cast<u64 *>(gb);

@@ -1,19 +1,20 @@
 // K-b/K-c/K-d, direct-addressed strategy (dense products).
 //
-// Work split: the output rank interval [lo, end) is cut into G groups at
-// order statistics of the almost regular grid of Sec. 5 (each grid point
-// gamma_{i,j} stands for the same number of term products, so equal numbers
-// of sorted grid points per group give groups with about equal operation
-// counts, as the paper's first step intends).  One CTA owns one group, so no
-// two CTAs ever write the same output term (Alg. 1, second step).
+// Work split: the output rank interval [lo, end) is cut into G groups with
+// about equal cost.  Cost is sampled by the almost regular grid of Sec. 5
+// (each grid point gamma_{i,j} stands for the same number of term products,
+// as the paper's first step intends) plus a per-rank cost for the slots a
+// CTA clears and scans; both go into a histogram over the interval, and the
+// group boundaries sit where its cumulative cost crosses m / G of the total.
+// One CTA owns one group, so no two CTAs ever write the same output term
+// (Alg. 1, second step).
 //
 // Inside a group the CTA slides a window [lo, hi) of at most `slots` ranks
-// and keeps one shared-memory accumulator per rank.  For each window it
-// needs, per row i of the pp-matrix, the first column with
-// gamma_{i,j} >= lo and the first with gamma_{i,j} >= hi (FindEdge,
-// Sec. 2).  Both edges move left as i grows, so each thread walks a
-// contiguous chunk of rows as a staircase (O(n_a + n_b) per window for the
-// whole CTA) after one binary search for its first row.
+// and keeps one shared-memory accumulator per rank.  Each window needs, per
+// row i of the pp-matrix, the first column with gamma_{i,j} >= lo and the
+// first with gamma_{i,j} >= hi (FindEdge, Sec. 2); a separate kernel
+// computes them for every window boundary beforehand (k_find_edge), so the
+// accumulate kernel only reads them.
 #include "pm_direct.cuh"
 
 namespace pm {
@@ -41,12 +42,6 @@ __device__ __forceinline__ DTables carve_dtables(unsigned char *p)
     return t;
 }
 
-// residue of a slot: 64-bit sum plus 8 per wrap of the sum
-__device__ __forceinline__ u64 m61_slot(u64 sum, u32 nwraps)
-{
-    return m61_reduce(m61_reduce(sum) + 8ull * nwraps);
-}
-
 __device__ __forceinline__ u32 d_row_of(const u32 *off, u32 nrows, u32 p)
 {
     u32 lo = 0, len = nrows;
@@ -62,11 +57,30 @@ __device__ __forceinline__ u32 d_row_of(const u32 *off, u32 nrows, u32 p)
     return lo - 1;
 }
 
+// first index in [0, n) with a[i] >= x (n if none); u32 or u64 keys, in
+// shared or global memory
+template <class K>
+__device__ __forceinline__ u32 lower_bound_k(const K *a, u32 n, u64 x)
+{
+    u32 lo = 0, len = n;
+    while (len > 0) {
+        u32 half = len >> 1;
+        if ((u64)a[lo + half] < x) {
+            lo += half + 1;
+            len -= half + 1;
+        } else {
+            len = half;
+        }
+    }
+    return lo;
+}
+
 // lower_bound(B, x) when it is known to be <= j: a short linear check, then a
 // galloping search downwards (O(log of the distance moved))
-__device__ __forceinline__ u32 walk_down(const u64 *__restrict__ B, u32 j, u64 x)
+template <class K>
+__device__ __forceinline__ u32 walk_down(const K *B, u32 j, u64 x)
 {
-    if (j == 0 || __ldg(B + j - 1) < x) return j;
+    if (j == 0 || (u64)B[j - 1] < x) return j;
     u32 hi = j - 1;  // B[hi] >= x
     u32 step = 1, lo;
     for (;;) {
@@ -75,97 +89,246 @@ __device__ __forceinline__ u32 walk_down(const u64 *__restrict__ B, u32 j, u64 x
             break;
         }
         const u32 probe = hi - step;
-        if (__ldg(B + probe) < x) {
+        if ((u64)B[probe] < x) {
             lo = probe + 1;
             break;
         }
         hi = probe;
         step <<= 1;
     }
-    return lo + lower_bound_u64(B + lo, hi - lo, x);
+    return lo + lower_bound_k(B + lo, hi - lo, x);
 }
 
-// E0[i] = lower_bound(B, lo - A_i), E1[i] = lower_bound(B, hi - A_i) for rows
-// i in [i0, i1); every such row has A_i + B_min < hi.  Returns the number of
-// term products of this thread's rows inside [lo, hi).
-__device__ __forceinline__ u64 staircase_edges(const u64 *__restrict__ A, const u64 *__restrict__ B, u32 nb,
-                                               u32 i0, u32 i1, u64 lo, u64 hi, u32 *__restrict__ E0,
-                                               u32 *__restrict__ E1)
+// FindEdge (Sec. 2) for the window boundaries: for boundary x = W[b] and
+// every row i that reaches it, E[b][i] = #{j : beta_j < x - alpha_i}.  Rows
+// below i0 (alpha_i + beta_max < x) have all n_b columns below x, rows from
+// i1 on (alpha_i + beta_min >= x) none; cnt[b] = #{(i, j) : gamma_ij < x}.
+// The row edges move left as i grows, so each thread walks a contiguous
+// chunk of rows as a staircase after one binary search; g's keys are
+// staged in shared memory when they fit.
+template <class K>
+__global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const K *__restrict__ B, u32 na, u32 nb,
+                                                  const u64 *__restrict__ W, const u64 *__restrict__ nbound_minus1,
+                                                  u32 *__restrict__ E, u32 *__restrict__ i0s,
+                                                  u32 *__restrict__ i1s, u64 *__restrict__ cnt, u32 stage)
 {
-    const u32 rows = i1 - i0;
-    const u32 per = (rows + DT - 1) / DT;
-    const u32 r0 = i0 + threadIdx.x * per;
-    const u32 r1 = min(r0 + per, i1);
-    if (r0 >= r1) return 0;
-    u64 a = __ldg(A + r0);
-    u32 j0 = lo > a ? lower_bound_u64(B, nb, lo - a) : 0u;
-    u32 j1 = lower_bound_u64(B, nb, hi - a);
-    E0[r0] = j0;
-    E1[r0] = j1;
-    u64 sum = j1 - j0;
-    for (u32 i = r0 + 1; i < r1; i++) {
-        a = __ldg(A + i);
-        j0 = lo <= a ? 0u : walk_down(B, j0, lo - a);
-        j1 = walk_down(B, j1, hi - a);
-        E0[i] = j0;
-        E1[i] = j1;
-        sum += j1 - j0;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u64 ws[32];
+    __shared__ u32 rows[2];
+    K *Bs = (K *)smem;
+    if (stage)
+        for (u32 j = threadIdx.x; j < nb; j += DT) Bs[j] = B[j];
+    __syncthreads();
+    const K *Bp = stage ? Bs : B;
+    const u64 bmin = (u64)B[0], bmax = (u64)B[nb - 1];
+    const u64 nbound = *nbound_minus1 + 1;
+    for (u64 b = blockIdx.x; b < nbound; b += gridDim.x) {
+        const u64 x = W[b];
+        if (threadIdx.x == 0) {
+            rows[0] = x > bmax ? lower_bound_k(A, na, x - bmax) : 0u;
+            rows[1] = x > bmin ? lower_bound_k(A, na, x - bmin) : 0u;
+        }
+        __syncthreads();
+        const u32 i0 = rows[0], i1 = rows[1];
+        u32 *Eb = E + b * na;
+        u64 sum = 0;
+        const u32 per = (i1 - i0 + DT - 1) / DT;
+        const u32 r0 = i0 + threadIdx.x * per;
+        const u32 r1 = min(r0 + per, i1);
+        if (r0 < r1) {
+            u32 j = lower_bound_k(Bp, nb, x - (u64)A[r0]);
+            Eb[r0] = j;
+            sum = j;
+            for (u32 i = r0 + 1; i < r1; i++) {
+                j = walk_down(Bp, j, x - (u64)A[i]);
+                Eb[i] = j;
+                sum += j;
+            }
+        }
+        u64 total;
+        block_exclusive_scan(sum, total, ws);
+        if (threadIdx.x == 0) {
+            cnt[b] = total + (u64)i0 * nb;
+            i0s[b] = i0;
+            i1s[b] = i1;
+        }
+        __syncthreads();
     }
-    return sum;
 }
 
-template <int KIND>
+// windows of at most `slots` ranks inside each group
+__global__ void k_window_count(const u64 *__restrict__ gb, u32 G, u32 slots, u64 *__restrict__ nw)
+{
+    u32 g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    const u64 span = gb[g + 1] - gb[g];
+    nw[g] = (span + slots - 1) / slots;
+}
+
+__global__ void k_window_bounds(const u64 *__restrict__ gb, u32 G, u32 slots, const u64 *__restrict__ wpos,
+                                u64 *__restrict__ W)
+{
+    u32 g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= G) return;
+    for (u64 k = 0, n = wpos[g + 1] - wpos[g]; k < n; k++) W[wpos[g] + k] = gb[g] + k * slots;
+    if (g == G - 1) W[wpos[G]] = gb[G];
+}
+
+// One product stream of a lane: flattened index p in [p, end) of the pass,
+// with its row's data cached in registers.
+struct Stream {
+    u32 p, end, r, rend, jbase, ra;
+    u64 ca;
+};
+
+__device__ __forceinline__ void stream_load_row(Stream &c, const DTables &t, u32 lo32)
+{
+    c.rend = t.off[c.r + 1];
+    c.jbase = t.jlo[c.r] - t.off[c.r];
+    c.ra = t.ra[c.r] - lo32;
+    c.ca = t.ca[c.r];
+}
+
+__device__ __forceinline__ void stream_init(Stream &c, const DTables &t, u32 nrows, u32 p, u32 end, u32 lo32)
+{
+    c.p = p;
+    c.end = end;
+    if (p < end) {
+        c.r = d_row_of(t.off, nrows, p);
+        stream_load_row(c, t, lo32);
+    }
+}
+
+__device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t, u32 lo32)
+{
+    if (c.p >= c.rend) {
+        do {
+            c.r++;
+        } while (t.off[c.r + 1] <= c.p);
+        stream_load_row(c, t, lo32);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory accumulators, one slot per rank of the window
+//   ACC_W64: mod p; a 64-bit sum and a 32-bit count of its wraps
+//            (2^64 = 8 mod p), 12 bytes per slot;
+//   ACC_L16: mod p; the lazily reduced product (< 2^62) split into four
+//            16-bit limbs, each added into its own 32-bit counter with a
+//            fire-and-forget reduction (one bank word each, no return
+//            value); exact while a slot receives at most 65537 products,
+//            i.e. when min(n_f, n_g) <= 65537 (one product per row and
+//            per column at most), 16 bytes per slot;
+//   ACC_I128: int64 inputs; 128-bit sum as lo and hi words, 16 bytes.
+// ---------------------------------------------------------------------------
+enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2 };
+
+template <int ACC>
+struct Acc {
+    static constexpr u32 bytes = ACC == ACC_W64 ? 12 : 16;
+    u64 *w;      // ACC_W64: sums; ACC_I128: lo words [0, slots), hi words [slots, 2 slots)
+    u32 *c;      // ACC_W64: wrap counts; ACC_L16: limb counters, limb k at [k * slots, (k+1) * slots)
+    u32 slots;
+
+    __device__ __forceinline__ void carve(unsigned char *p, u32 n)
+    {
+        slots = n;
+        w = (u64 *)p;
+        c = ACC == ACC_W64 ? (u32 *)(w + n) : (u32 *)p;
+    }
+    __device__ __forceinline__ void zero(u32 s)
+    {
+        if (ACC == ACC_W64) {
+            w[s] = 0;
+            c[s] = 0;
+        } else if (ACC == ACC_L16) {
+            c[s] = 0;
+            c[slots + s] = 0;
+            c[2 * slots + s] = 0;
+            c[3 * slots + s] = 0;
+        } else {
+            w[s] = 0;
+            w[slots + s] = 0;
+        }
+    }
+    __device__ __forceinline__ void add(u32 s, u64 a, u64 b)
+    {
+        if (ACC == ACC_W64) {
+            const u64 v = m61_mul_lazy(a, b);
+            const u64 old = atomicAdd(&w[s], v);
+            atomicAdd(&c[s], (u32)(old + v < old));
+        } else if (ACC == ACC_L16) {
+            const u64 v = m61_mul_lazy(a, b);
+            atomicAdd(&c[s], (u32)v & 0xFFFFu);
+            atomicAdd(&c[slots + s], (u32)(v >> 16) & 0xFFFFu);
+            atomicAdd(&c[2 * slots + s], (u32)(v >> 32) & 0xFFFFu);
+            atomicAdd(&c[3 * slots + s], (u32)(v >> 48));
+        } else {
+            u64 plo, phi;
+            mul_i64_wide((i64)a, (i64)b, plo, phi);
+            const u64 old = atomicAdd(&w[s], plo);
+            atomicAdd(&w[slots + s], phi + (old + plo < old ? 1ull : 0ull));
+        }
+    }
+    // the slot's value: residue mod p (v1 = 0), or the int128 (v0, v1)
+    __device__ __forceinline__ bool value(u32 s, u64 &v0, u64 &v1) const
+    {
+        if (ACC == ACC_W64) {
+            v0 = m61_reduce(m61_reduce(w[s]) + 8ull * c[s]);
+            v1 = 0;
+            return v0 != 0;
+        } else if (ACC == ACC_L16) {
+            // sum = L0 + L1 2^16 + L2 2^32 + L3 2^48 with L_k < 2^32
+            const u64 l0 = c[s], l1 = c[slots + s], l2 = c[2 * slots + s], l3 = c[3 * slots + s];
+            u64 lo = l0 + (l1 << 16);               // < 2^49
+            u64 hi = 0;
+            add128(lo, hi, l2 << 32, l2 >> 32);
+            add128(lo, hi, l3 << 48, l3 >> 16);
+            // 2^64 = 8 (mod p); hi < 2^17
+            v0 = m61_reduce(m61_reduce(lo) + 8ull * hi);
+            v1 = 0;
+            return v0 != 0;
+        } else {
+            v0 = w[s];
+            v1 = w[slots + s];
+            return (v0 | v1) != 0;
+        }
+    }
+};
+
+template <int ACC>
 __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
-    __shared__ u32 win[2];
-    // M61: 64-bit sums [0, slots) then 32-bit wrap counts; I64: lo words
-    // [0, slots) then hi words [slots, 2 slots)
-    u64 *acc = (u64 *)smem;
-    u32 *wraps = (u32 *)(acc + slots);
-    DTables t = carve_dtables(smem + (size_t)slots * (KIND == PM_COEF_M61 ? 12 : 16));
+    Acc<ACC> acc;
+    acc.carve(smem, slots);
+    DTables t = carve_dtables(smem + (size_t)slots * Acc<ACC>::bytes);
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const u32 g = blockIdx.x;
     if (g >= a.ngroups) return;
-    const u64 glo = a.gb[g], ghi = a.gb[g + 1];
-    u32 *E0 = a.edges + (size_t)g * 2 * a.na;
-    u32 *E1 = E0 + a.na;
-    const u64 bmin = __ldg(a.B), bmax = __ldg(a.B + a.nb - 1);
-    const u64 obase = glo - a.lo;
+    const u64 obase = a.gb[g] - a.lo;
+    const u32 nb = a.nb, na = a.na;
     u64 run = 0;
 
-    for (u64 lo = glo; lo < ghi;) {
-        const u64 hi = ghi - lo > slots ? lo + slots : ghi;
+    for (u64 bw = a.wpos[g], bend = a.wpos[g + 1]; bw < bend; bw++) {
+        const u64 lo = a.W[bw], hi = a.W[bw + 1];
         const u32 span = (u32)(hi - lo);
-        if (tid == 0) {
-            win[0] = lo > bmax ? lower_bound_u64(a.A, a.na, lo - bmax) : 0u;
-            win[1] = lower_bound_u64(a.A, a.na, hi - bmin);
-        }
-        __syncthreads();
-        const u32 i0 = win[0], i1 = win[1];
-        u64 wprod = 0;
-        if (i0 < i1) {
-            u64 mine = staircase_edges(a.A, a.B, a.nb, i0, i1, lo, hi, E0, E1);
-            block_exclusive_scan(mine, wprod, ws);  // also orders the edge writes before their reads
-        }
-        if (wprod == 0) {  // no term product lands in this window
-            __syncthreads();  // every thread has read win[] before it is rewritten
-            lo = hi;
-            continue;
-        }
-        for (u32 s = tid; s < span; s += DT) {
-            acc[s] = 0;
-            if (KIND == PM_COEF_M61) wraps[s] = 0;
-            else acc[slots + s] = 0;
-        }
+        if (a.cnt[bw + 1] == a.cnt[bw]) continue;  // no term product lands in this window
+        // rows reaching the window: [i0(lo), i1(hi)); edges below i1(lo) and
+        // from i0(hi) on are stored, the others are 0 and n_b
+        const u32 i0 = a.i0s[bw], i1 = a.i1s[bw + 1];
+        const u32 i1lo = a.i1s[bw], i0hi = a.i0s[bw + 1];
+        const u32 *Elo = a.E + bw * na, *Ehi = Elo + na;
+        for (u32 s = tid; s < span; s += DT) acc.zero(s);
         __syncthreads();
 
         for (u32 base = i0; base < i1; base += DROWS) {
             const u32 i = base + tid;
             u64 len = 0;
             if (i < i1) {
-                const u32 jl = E0[i], jh = E1[i];
+                const u32 jl = i < i1lo ? Elo[i] : 0u;
+                const u32 jh = i >= i0hi ? Ehi[i] : nb;
                 len = jh - jl;
                 t.ra[tid] = (u32)__ldg(a.A + i);
                 t.ca[tid] = __ldg(a.Ac + i);
@@ -178,45 +341,38 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             const u32 nrows = min(i1 - base, (u32)DROWS);
             __syncthreads();
 
-            // warp w takes a contiguous slice of the pass's products; a lane
-            // keeps its current row's data in registers
+            // warp w takes a contiguous slice of the pass's products; each
+            // lane runs two independent streams over its two halves so the
+            // loads and multiplies of one overlap the latency of the other
             const u32 tot = (u32)total;
-            const u32 per_warp = ((tot + DW - 1) / DW + 31u) & ~31u;
+            const u32 per_warp = ((tot + DW - 1) / DW + 63u) & ~63u;
             const u32 p0 = w * per_warp;
             const u32 p1 = min(p0 + per_warp, tot);
-            u32 p = p0 + lane;
-            if (p < p1) {
-                u32 r = d_row_of(t.off, nrows, p);
-                const u32 lo32 = (u32)lo;
-                u32 rend = t.off[r + 1];
-                u32 jbase = t.jlo[r] - t.off[r];
-                u32 ra = t.ra[r] - lo32;
-                u64 ca = t.ca[r];
-                for (; p < p1; p += 32) {
-                    if (p >= rend) {
-                        do {
-                            r++;
-                        } while (t.off[r + 1] <= p);
-                        rend = t.off[r + 1];
-                        jbase = t.jlo[r] - t.off[r];
-                        ra = t.ra[r] - lo32;
-                        ca = t.ca[r];
-                    }
-                    const u32 j = jbase + p;
-                    const u32 slot = ra + __ldg(a.B32 + j);
-                    if (KIND == PM_COEF_M61) {
-                        // 2^64 = 8 (mod p): count the 64-bit word's wraps
-                        // beside it instead of repairing them in a loop
-                        const u64 v = m61_mul_lazy(ca, __ldg(a.Bc + j));
-                        const u64 old = atomicAdd(&acc[slot], v);
-                        atomicAdd(&wraps[slot], (u32)(old + v < old));
-                    } else {
-                        u64 plo, phi;
-                        mul_i64_wide((i64)ca, (i64)__ldg(a.Bc + j), plo, phi);
-                        const u64 old = atomicAdd(&acc[slot], plo);
-                        atomicAdd(&acc[slots + slot], phi + (old + plo < old ? 1ull : 0ull));
-                    }
+            const u32 pm = min(p0 + per_warp / 2, p1);
+            const u32 lo32 = (u32)lo;
+            Stream sa, sb;
+            stream_init(sa, t, nrows, p0 + lane, pm, lo32);
+            stream_init(sb, t, nrows, pm + lane, p1, lo32);
+            while (sa.p < sa.end || sb.p < sb.end) {
+                const bool va = sa.p < sa.end, vb = sb.p < sb.end;
+                u32 ja = 0, jb = 0, ba = 0, bb = 0;
+                u64 ga = 0, gbv = 0;
+                if (va) {
+                    stream_advance_row(sa, t, lo32);
+                    ja = sa.jbase + sa.p;
+                    ba = __ldg(a.B32 + ja);
+                    ga = __ldg(a.Bc + ja);
                 }
+                if (vb) {
+                    stream_advance_row(sb, t, lo32);
+                    jb = sb.jbase + sb.p;
+                    bb = __ldg(a.B32 + jb);
+                    gbv = __ldg(a.Bc + jb);
+                }
+                if (va) acc.add(sa.ra + ba, sa.ca, ga);
+                if (vb) acc.add(sb.ra + bb, sb.ca, gbv);
+                sa.p += 32;
+                sb.p += 32;
             }
             __syncthreads();
         }
@@ -230,7 +386,8 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         for (u32 sb = s0; sb < s1; sb += 32) {
             const u32 s = sb + lane;
             bool nz = false;
-            if (s < s1) nz = KIND == PM_COEF_M61 ? m61_slot(acc[s], wraps[s]) != 0 : (acc[s] | acc[slots + s]) != 0;
+            u64 x0, x1;
+            if (s < s1) nz = acc.value(s, x0, x1);
             wcount += __popc(__ballot_sync(0xffffffffu, nz));
         }
         u64 wtot;
@@ -240,21 +397,12 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             const u32 s = sb + lane;
             u64 v0 = 0, v1 = 0;
             bool nz = false;
-            if (s < s1) {
-                if (KIND == PM_COEF_M61) {
-                    v0 = m61_slot(acc[s], wraps[s]);
-                    nz = v0 != 0;
-                } else {
-                    v0 = acc[s];
-                    v1 = acc[slots + s];
-                    nz = (v0 | v1) != 0;
-                }
-            }
+            if (s < s1) nz = acc.value(s, v0, v1);
             const u32 bal = __ballot_sync(0xffffffffu, nz);
             if (nz) {
                 const u64 d = put + __popc(bal & ((1u << lane) - 1u));
                 a.okey[d] = rank_to_key(a.L, lo + s);
-                if (KIND == PM_COEF_M61) {
+                if (ACC != ACC_I128) {
                     a.ocoef[d] = v0;
                 } else {
                     a.ocoef[2 * d] = v0;
@@ -265,33 +413,120 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         }
         run += wtot;
         __syncthreads();
-        lo = hi;
     }
     if (tid == 0) a.ucount[g] = run;
 }
 
-// group boundaries at order statistics of the sorted grid sample
-__global__ void k_group_bounds(const u64 *__restrict__ sample, u64 ns, u32 G, u64 lo, u64 end, u64 *__restrict__ gb)
+// Weighted histogram of the cost samples over NBK buckets of [lo, end):
+// every grid point of Sec. 5 (steps si, sj, alternate rows shifted by
+// `stagger`, plus the last row and column) adds wg to its bucket.
+__global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, u32 si, u32 sj,
+                            u32 stagger, u32 R, u32 Cc, u64 total, u64 lo, u64 bw, u64 nbk, u64 wg,
+                            u64 *__restrict__ hist)
+{
+    u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= total) return;
+    u64 i, j;
+    if (p < (u64)R * Cc) {
+        const u64 r = p / Cc, q = p % Cc;
+        i = r * si;
+        j = (r & 1) * stagger + q * sj;
+    } else if (p < (u64)R * Cc + Cc) {
+        i = na - 1;
+        j = (p - (u64)R * Cc) * sj;
+    } else {
+        i = (p - (u64)R * Cc - Cc) * si;
+        j = nb - 1;
+    }
+    if (i > na - 1) i = na - 1;
+    if (j > nb - 1) j = nb - 1;
+    u64 k = (A[i] + B[j] - lo) / bw;
+    if (k >= nbk) k = nbk - 1;
+    atomicAdd(&hist[k], wg);
+}
+
+// every bucket also carries the cost of the slots it spans
+__global__ void k_hist_add(u64 *__restrict__ hist, u64 nbk, u64 wu)
+{
+    u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nbk) hist[k] += wu;
+}
+
+// group m starts at the first bucket whose cumulative cost reaches m W / G
+__global__ void k_group_bounds(const u64 *__restrict__ cw, u64 nbk, u32 G, u64 lo, u64 end, u64 bw,
+                               u64 *__restrict__ gb)
 {
     u32 m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m > G) return;
     u64 v;
-    if (m == 0) v = lo;
-    else if (m == G) v = end;
-    else v = sample[(u64)(((unsigned __int128)m * ns) / G)];
+    if (m == 0) {
+        v = lo;
+    } else if (m == G) {
+        v = end;
+    } else {
+        const u64 W = cw[nbk];
+        const u64 target = (u64)(((unsigned __int128)W * m) / G);
+        u64 k = lower_bound_u64(cw, (u32)(nbk + 1), target);
+        if (k > nbk) k = nbk;
+        v = lo + k * bw;
+        if (v > end) v = end;
+    }
     gb[m] = v;
 }
 
-size_t direct_smem_bytes(u32 slots, int kind)
+u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
+                   u32 grid_l, u64 products, double slot_cost)
 {
-    return (size_t)slots * (kind == PM_COEF_M61 ? 12 : 16) + DTABLE_BYTES;
+    // cost model: a grid point of the pp-matrix stands for products / ng
+    // term products; a rank of the interval for slot_cost (clearing,
+    // scanning and edge finding of its slot)
+    u32 l = grid_l ? grid_l : 1;
+    u32 si = na / l ? na / l : 1, sj = nb / l ? nb / l : 1;
+    u32 stagger = (u32)(nb / (2ull * l));
+    u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
+    const u64 ng = (u64)R * Cc + Cc + R;
+    const u64 span = end - lo;
+    const u64 nbk = span < 65536 ? span : 65536;
+    const u64 bw = (span + nbk - 1) / nbk;
+    u64 *hist = S.get<u64>(nbk), *cw = S.get<u64>(nbk + 1);
+    PM_CUDA(cudaMemsetAsync(hist, 0, nbk * 8, c.s));
+    const u64 wg = products / ng + 1;
+    const u64 wu = (u64)(slot_cost * (double)bw) + 1;
+    k_grid_hist<<<(unsigned)((ng + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, ng, lo, bw, nbk,
+                                                               wg, hist);
+    PM_LAUNCHED(c);
+    k_hist_add<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(hist, nbk, wu);
+    PM_LAUNCHED(c);
+    scan_exclusive_u64(c, S, hist, cw, nbk);
+    u64 *gb = S.get<u64>(G + 1);
+    k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cw, nbk, G, lo, end, bw, gb);
+    PM_LAUNCHED(c);
+    return gb;
 }
 
-u32 direct_max_slots(int kind)
+static int acc_policy(int kind, u64 min_n, int requested)
+{
+    if (kind != PM_COEF_M61) return ACC_I128;
+    if (requested == PM_ACC_WIDE) return ACC_W64;
+    if (requested == PM_ACC_LIMBS) {
+        if (min_n > 65537) throw Error(PM_EINVAL, "limb accumulators need min(n_f, n_g) <= 65537");
+        return ACC_L16;
+    }
+    return min_n <= 65537 ? ACC_L16 : ACC_W64;
+}
+
+static u32 acc_bytes(int acc) { return acc == ACC_W64 ? 12 : 16; }
+
+size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested)
+{
+    return (size_t)slots * acc_bytes(acc_policy(kind, min_n, requested)) + DTABLE_BYTES;
+}
+
+u32 direct_max_slots(int kind, u64 min_n, int requested)
 {
     // 227 KB of opt-in shared memory per CTA, minus tables and static use
     size_t avail = 227 * 1024 - DTABLE_BYTES - 512;
-    return (u32)(avail / (kind == PM_COEF_M61 ? 12 : 16)) & ~1023u;
+    return (u32)(avail / acc_bytes(acc_policy(kind, min_n, requested))) & ~1023u;
 }
 
 template <class K>
@@ -300,32 +535,57 @@ static void set_smem(K kernel, size_t bytes)
     PM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l)
-{
-    u32 l = grid_l ? grid_l : 1;
-    u32 si = na / l ? na / l : 1, sj = nb / l ? nb / l : 1;
-    u32 stagger = (u32)(nb / (2ull * l));
-    u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
-    u64 total = (u64)R * Cc + Cc + R;
-    u64 *cand = S.get<u64>(total);
-    grid_sample(c, A, na, B, nb, si, sj, stagger, R, Cc, total, cand);
-    radix_sort_pairs(c, S, cand, nullptr, nullptr, total, bit_length(end));
-    u64 *gb = S.get<u64>(G + 1);
-    k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cand, total, G, lo, end, gb);
-    PM_LAUNCHED(c);
-    return gb;
-}
 
-void launch_direct(Ctx &c, const DirectArgs &a, u32 slots, int kind)
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end)
 {
-    size_t bytes = direct_smem_bytes(slots, kind);
-    if (kind == PM_COEF_M61) {
-        set_smem(k_direct<PM_COEF_M61>, bytes);
-        k_direct<PM_COEF_M61><<<a.ngroups, DT, bytes, c.s>>>(a, slots);
+    const u32 G = a.ngroups;
+    // window boundaries W (at most G + span / slots + 1 of them)
+    u64 *nw = S.get<u64>(G);
+    u64 *wpos = S.get<u64>(G + 1);
+    k_window_count<<<(G + 255) / 256, 256, 0, c.s>>>(a.gb, G, slots, nw);
+    PM_LAUNCHED(c);
+    scan_exclusive_u64(c, S, nw, wpos, G);
+    const u64 nbmax = G + (end - a.lo + slots - 1) / slots + 1;
+    u64 *W = S.get<u64>(nbmax);
+    k_window_bounds<<<(G + 255) / 256, 256, 0, c.s>>>(a.gb, G, slots, wpos, W);
+    PM_LAUNCHED(c);
+    if (nbmax * a.na > (2ull << 30)) throw Error(PM_ENOMEM, "edge table too large");
+    a.W = W;
+    a.wpos = wpos;
+    a.E = S.get<u32>(nbmax * a.na);
+    a.i0s = S.get<u32>(nbmax);
+    a.i1s = S.get<u32>(nbmax);
+    a.cnt = S.get<u64>(nbmax);
+
+    // FindEdge at every boundary
+    const unsigned fgrid = (unsigned)(nbmax < (u64)c.sm_count * 4 ? nbmax : (u64)c.sm_count * 4);
+    if (a.A32) {
+        const size_t sb = (size_t)a.nb * 4;
+        const u32 stage = sb <= 200 * 1024;
+        set_smem(k_find_edge<u32>, stage ? sb : 0);
+        k_find_edge<u32><<<fgrid, DT, stage ? sb : 0, c.s>>>(a.A32, a.B32, a.na, a.nb, W, wpos + G, a.E, a.i0s,
+                                                             a.i1s, a.cnt, stage);
     } else {
-        set_smem(k_direct<PM_COEF_I64_ACC128>, bytes);
-        k_direct<PM_COEF_I64_ACC128><<<a.ngroups, DT, bytes, c.s>>>(a, slots);
+        const size_t sb = (size_t)a.nb * 8;
+        const u32 stage = sb <= 200 * 1024;
+        set_smem(k_find_edge<u64>, stage ? sb : 0);
+        k_find_edge<u64><<<fgrid, DT, stage ? sb : 0, c.s>>>(a.A, a.B, a.na, a.nb, W, wpos + G, a.E, a.i0s, a.i1s,
+                                                             a.cnt, stage);
+    }
+    PM_LAUNCHED(c);
+
+    // accumulate, one CTA per group
+    const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
+    const size_t bytes = (size_t)slots * acc_bytes(acc) + DTABLE_BYTES;
+    if (acc == ACC_W64) {
+        set_smem(k_direct<ACC_W64>, bytes);
+        k_direct<ACC_W64><<<G, DT, bytes, c.s>>>(a, slots);
+    } else if (acc == ACC_L16) {
+        set_smem(k_direct<ACC_L16>, bytes);
+        k_direct<ACC_L16><<<G, DT, bytes, c.s>>>(a, slots);
+    } else {
+        set_smem(k_direct<ACC_I128>, bytes);
+        k_direct<ACC_I128><<<G, DT, bytes, c.s>>>(a, slots);
     }
     PM_LAUNCHED(c);
 }

@@ -10,20 +10,25 @@ struct DirectArgs {
     const u64 *A, *Ac;   // f: ranks (sorted), coefficients
     const u64 *B, *Bc;   // g
     const u32 *B32;      // low 32 bits of g's ranks (slot arithmetic is mod 2^32)
+    const u32 *A32;      // f's ranks as u32 when the whole box fits in 32 bits, else null
     u32 na, nb;
     const u64 *gb;       // G + 1 group boundaries (ranks)
     u32 ngroups;
     u64 lo;              // smallest product rank; group g writes from gb[g] - lo
-    u32 *edges;          // scratch: 2 * na words per group
+    const u64 *W;        // window boundaries; group g owns windows [wpos[g], wpos[g+1])
+    const u64 *wpos;
+    u32 *E;              // FindEdge table: E[b * na + i] for boundary b, row i
+    u32 *i0s, *i1s;      // per boundary: first row reaching it, first row past it
+    u64 *cnt;            // per boundary: term products with rank below it
     u64 *okey, *ocoef;   // output scratch
     u64 *ucount;         // terms written per group
     Layout L;
 };
 
-size_t direct_smem_bytes(u32 slots, int kind);
-u32 direct_max_slots(int kind);
+size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
+u32 direct_max_slots(int kind, u64 min_n, int requested);
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l);
-void launch_direct(Ctx &c, const DirectArgs &a, u32 slots, int kind);
+                   u32 grid_l, u64 products, double slot_cost);
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end);
 
 }  // namespace pm

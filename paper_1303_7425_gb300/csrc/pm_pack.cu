@@ -194,6 +194,91 @@ void canonicalize(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &raw, 
     PM_CUDA(cudaMemcpyAsync(d_count, pos + n, sizeof(u64), cudaMemcpyDeviceToDevice, c.s));
 }
 
+
+// ---------------------------------------------------------------------------
+// dense canonicalisation: when an operand's own exponent box is small, each
+// term is added into the slot of its rank (repeated monomials combine in the
+// slot), then the non-zero slots are compacted in rank order, which is the
+// monomial order.  M61: 64-bit sum + 32-bit wrap count (2^64 = 8 mod p);
+// I64: 128-bit sum as lo/hi words.
+// ---------------------------------------------------------------------------
+
+__global__ void k_dense_scatter(const u32 *__restrict__ exps, const void *__restrict__ coefs, size_t n, Layout L,
+                                int kind, u64 *__restrict__ sum, u64 *__restrict__ aux)
+{
+    size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    u64 r = 0;
+    for (u32 v = 0; v < L.nv; v++) r += (u64)exps[t * L.nv + v] * L.stride[v];
+    const u64 c = ((const u64 *)coefs)[t];
+    if (kind == PM_COEF_M61) {
+        const u64 x = m61_reduce(c);
+        const u64 old = atomicAdd(&sum[r], x);
+        if (old + x < old) atomicAdd((u32 *)aux + r, 1u);
+    } else {
+        const u64 hi = (u64)((i64)c >> 63);
+        const u64 old = atomicAdd(&sum[r], c);
+        atomicAdd(&aux[r], hi + (old + c < old ? 1ull : 0ull));
+    }
+}
+
+__device__ __forceinline__ bool dense_value(const u64 *sum, const u64 *aux, u64 s, int kind, u64 &v, u32 *status)
+{
+    if (kind == PM_COEF_M61) {
+        v = m61_reduce(m61_reduce(sum[s]) + 8ull * ((const u32 *)aux)[s]);
+        return v != 0;
+    }
+    const u64 lo = sum[s], hi = aux[s];
+    if (hi != (u64)((i64)lo >> 63) && status) atomicOr(status, ST_COEF_BOUND);  // must fit int64
+    v = lo;
+    return (lo | hi) != 0;
+}
+
+__global__ void k_dense_flags(const u64 *__restrict__ sum, const u64 *__restrict__ aux, u64 box, int kind,
+                              u64 *__restrict__ flag, u32 *__restrict__ status)
+{
+    u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= box) return;
+    u64 v;
+    flag[s] = dense_value(sum, aux, s, kind, v, status) ? 1ull : 0ull;
+}
+
+__global__ void k_dense_emit(const u64 *__restrict__ sum, const u64 *__restrict__ aux, u64 box, int kind,
+                             const u64 *__restrict__ flag, const u64 *__restrict__ pos, Layout L,
+                             u64 *__restrict__ okey, u64 *__restrict__ ocoef)
+{
+    u64 s = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= box || !flag[s]) return;
+    u64 v;
+    dense_value(sum, aux, s, kind, v, nullptr);
+    okey[pos[s]] = rank_to_key(L, s);
+    ocoef[pos[s]] = v;
+}
+
+void canonicalize_dense(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &own, u64 own_box, int kind,
+                        Operand &op, u32 *d_status, u64 *d_count)
+{
+    op.n = 0;
+    const size_t n = in.n;
+    u64 *sum = S.get<u64>(own_box), *aux = S.get<u64>(own_box);
+    PM_CUDA(cudaMemsetAsync(sum, 0, own_box * 8, c.s));
+    PM_CUDA(cudaMemsetAsync(aux, 0, own_box * 8, c.s));
+    k_dense_scatter<<<grid_for(n, 256), 256, 0, c.s>>>(in.exps, in.coefs, n, own, kind, sum, aux);
+    PM_LAUNCHED(c);
+    u64 *flag = S.get<u64>(own_box), *pos = S.get<u64>(own_box + 1);
+    k_dense_flags<<<grid_for(own_box, 256), 256, 0, c.s>>>(sum, aux, own_box, kind, flag, d_status);
+    PM_LAUNCHED(c);
+    scan_exclusive_u64(c, S, flag, pos, own_box);
+    const size_t cap = n < own_box ? n : own_box;
+    op.key = S.get<u64>(cap);
+    op.coef = S.get<u64>(cap);
+    op.rank = S.get<u64>(cap);
+    k_dense_emit<<<grid_for(own_box, 256), 256, 0, c.s>>>(sum, aux, own_box, kind, flag, pos, own, op.key,
+                                                          op.coef);
+    PM_LAUNCHED(c);
+    PM_CUDA(cudaMemcpyAsync(d_count, pos + own_box, sizeof(u64), cudaMemcpyDeviceToDevice, c.s));
+}
+
 void operand_stats(Ctx &c, const Operand &op, u64 n_max, const u64 *d_n, const Layout &L, int kind, u32 *d_maxe,
                    u64 *d_maxabs, u64 *d_first_last)
 {

@@ -22,6 +22,8 @@ pytestmark = pytest.mark.gpu
 STRATS = [
     dict(strategy="auto"),
     dict(strategy="direct"),
+    dict(strategy="direct", accumulator="wide"),
+    dict(strategy="direct", accumulator="limbs", slots=2048),
     dict(strategy="direct", slots=512),            # many ranges, ragged tails
     dict(strategy="direct", slots=1000, ranges_per_sm=64),
     dict(strategy="sort"),
@@ -49,7 +51,7 @@ def test_c1_exact(opts):
 
 
 @pytest.mark.parametrize("kind", ["m61", "i64"])
-@pytest.mark.parametrize("opts", STRATS[:5], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
+@pytest.mark.parametrize("opts", STRATS[:7], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
 def test_dense_reduced_exact(kind, opts):
     mons = polygen.monomials_total_degree(4, 10)          # 1001 monomials
     st = polygen.Stream(1234, 0)
@@ -85,11 +87,12 @@ def _sampled_check(w, gpu, nsample=120, seed=0):
 
 
 @pytest.mark.parametrize("kind", ["m61", "i64"])
-def test_c2_full_size(kind):
+@pytest.mark.parametrize("acc", ["auto", "wide"])
+def test_c2_full_size(kind, acc):
     """The dense workload at full size: 10626 x 10626 terms, exactly
     C(44, 4) = 135751 result terms, sampled coefficients, evaluation."""
     w = polygen.workload_c2(kind)
-    gpu = run_gpu(w.field_bits, kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    gpu = run_gpu(w.field_bits, kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, accumulator=acc)
     check_canonical(gpu[0], gpu[1], w.field_bits, kind)
     assert gpu[0].shape[0] == math.comb(44, 4)
     assert gpu[2]["term_products"] == 10626 ** 2
@@ -99,7 +102,8 @@ def test_c2_full_size(kind):
 def test_c3_reduced_exact():
     w = polygen.workload_c3(n=3000)
     ref = _oracle(w)
-    for opts in (dict(strategy="auto"), dict(strategy="sort"), dict(strategy="direct", slots=4096)):
+    for opts in (dict(strategy="auto"), dict(strategy="sort"), dict(strategy="direct", slots=4096),
+                 dict(strategy="direct", accumulator="wide")):
         gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
         assert_same(gpu, ref, w.field_bits)
 
