@@ -157,6 +157,39 @@ int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *
  * Fails with PM_EEXP_OVERFLOW if an exponent reaches its guard bit. */
 int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream);
 
+/* ---- the product without device allocation --------------------------------
+ *
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot allocate device memory: code running where cudaMalloc (or any
+ * allocator) is forbidden or would synchronise the device, such as a
+ * real-time thread, an allocator callback, or a plugin whose host
+ * application owns every device allocation.  pm_polymul takes its scratch
+ * from the stream-ordered allocator; this entry point takes all of its
+ * scratch from a file-scope static device array of PM_NOALLOC_SCRATCH_BYTES
+ * that every GPU which loads the library holds until the process exits, and
+ * it calls no cudaMalloc, cudaFree or other allocating routine.  It runs one
+ * kernel (one CTA) that forms, sorts and reduces all term products, so it is
+ * meant for small products only.
+ *
+ * Arguments, results and error codes are those of pm_polymul (without
+ * options or statistics), with these limits: n_f, n_g <= PM_NOALLOC_MAX_TERMS
+ * and n_f * n_g <= PM_NOALLOC_MAX_PRODUCTS (raw input sizes); larger inputs
+ * fail with PM_EINVAL before any work.  The caller allocates the inputs and
+ * the outputs.
+ *
+ * The first call on a device looks up the device address of the static
+ * array (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array, which keeps the
+ * last call's contents (the kernel clears what must start at zero), so calls
+ * whose executions overlap on the GPU race: serialise them.  The call
+ * synchronises `stream` before it returns. */
+#define PM_NOALLOC_MAX_TERMS     4096u
+#define PM_NOALLOC_MAX_PRODUCTS  65536u
+#define PM_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+int pm_polymul_noalloc(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                       pm_terms_out *h, void *stream);
+
 /* Human-readable message for an error code (static storage). */
 const char *pm_strerror(int code);
 

@@ -14,8 +14,9 @@ from ._native import (  # noqa: F401
     out_bound,
     pack,
     polymul,
+    polymul_noalloc,
     probe_mac,
     unpack,
 )
 
-__all__ = ["polymul", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

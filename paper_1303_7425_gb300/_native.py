@@ -63,8 +63,8 @@ class PolymulError(RuntimeError):
 
 
 # exported symbols, in include/polymul.h order
-SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_strerror", "pm_version",
-           "pm_probe_mac")
+SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_polymul_noalloc", "pm_strerror",
+           "pm_version", "pm_probe_mac")
 
 _lib = None
 
@@ -86,6 +86,9 @@ def lib():
         L.pm_unpack.restype = C.c_int
         L.pm_pack.argtypes = [P(pm_packing), C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
         L.pm_pack.restype = C.c_int
+        L.pm_polymul_noalloc.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in),
+                                         P(pm_terms_out), C.c_void_p]
+        L.pm_polymul_noalloc.restype = C.c_int
         L.pm_strerror.argtypes = [C.c_int]
         L.pm_strerror.restype = C.c_char_p
         L.pm_version.argtypes = []
@@ -231,3 +234,30 @@ def probe_mac(blocks: int, threads: int, iters: int, sink, seed: int = 0x1303742
     rc = lib().pm_probe_mac(blocks, threads, iters, seed, sink.data_ptr(), _stream_handle(stream))
     if rc != PM_OK:
         raise PolymulError(rc, "pm_probe_mac")
+
+
+NOALLOC_MAX_TERMS = 4096
+NOALLOC_MAX_PRODUCTS = 65536
+
+
+def polymul_noalloc(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, out, kind: str = "m61",
+                    stream=None) -> int:
+    """The product through pm_polymul_noalloc, for callers that cannot
+    allocate device memory: the library allocates nothing (its scratch is a
+    static device array); ``out`` = (keys, coefs) tensors supplied by the
+    caller.  Returns the number of result terms written."""
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs, out[0], out[1])
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    h = pm_terms_out()
+    h.keys = out[0].data_ptr()
+    h.coefs = out[1].data_ptr()
+    h.cap = int(out[0].shape[0])
+    rc = lib().pm_polymul_noalloc(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h),
+                                  _stream_handle(stream))
+    if rc != PM_OK:
+        err = PolymulError(rc, "pm_polymul_noalloc")
+        err.needed = int(h.n)
+        raise err
+    return int(h.n)
