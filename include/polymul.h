@@ -157,6 +157,62 @@ int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *
  * Fails with PM_EEXP_OVERFLOW if an exponent reaches its guard bit. */
 int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream);
 
+/* ---- batches of independent products (one device pass, a CUDA graph) ------
+ *
+ * Alg. 1 applied to every product of a batch in one pass: per operand,
+ * canonical form; per product, the grid splitters of Sec. 5 (first step);
+ * one persistent kernel whose CTAs take runs of consecutive output ranges
+ * from a device work counter (the dynamic scheduling of Sec. 2) and sort and
+ * reduce each range in shared memory; then per product the concatenation of
+ * its ranges.  No host synchronisation happens inside the pass, so it is
+ * captured once into a CUDA graph when the plan is created and each run
+ * replays that graph.  Every product uses the sort strategy.
+ *
+ * Limits: n_f, n_g <= PM_BATCH_MAX_TERMS per product (larger products belong
+ * to pm_polymul).  A plan keeps device pointers to the items' inputs and
+ * outputs: they must stay valid and unmoved while the plan is used; a run
+ * recomputes every product from the current contents of the inputs. */
+#define PM_BATCH_MAX_TERMS 8192u
+
+typedef struct pm_batch_item {
+    pm_packing pk;
+    int32_t coef_kind;         /* pm_coef_kind                                     */
+    pm_terms_in f, g;          /* device inputs, as for pm_polymul                 */
+    pm_terms_out h;            /* device outputs; h.n is written by finish          */
+    int32_t status;            /* written by finish: PM_OK or this item's error    */
+} pm_batch_item;
+
+typedef struct pm_batch_options {
+    uint32_t range_target;     /* term products per output range (64..3072;
+                                  default 1536)                                   */
+    uint32_t ranges_per_item;  /* consecutive ranges per work item (default 16)   */
+} pm_batch_options;
+
+typedef struct pm_batch_stats {
+    uint64_t term_products;    /* sum of n_f * n_g over the items                 */
+    uint64_t n_out;            /* result terms of the items that succeeded        */
+    uint64_t n_ranges;         /* output ranges over all items                    */
+    uint64_t work_items;       /* work-queue entries of the persistent kernel     */
+    uint32_t kernel_launches;  /* kernels per run                                 */
+    int32_t graph;             /* 1 when runs replay a CUDA graph                 */
+} pm_batch_stats;
+
+typedef struct pm_batch_plan pm_batch_plan;  /* opaque */
+
+/* Validate the items, allocate the plan's device memory (cudaMalloc; freed
+ * by pm_batch_plan_destroy) and capture the pass into a CUDA graph. */
+int pm_batch_plan_create(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                         pm_batch_plan **plan, void *stream);
+/* Launch the pass on `stream` (one graph launch; no host synchronisation). */
+int pm_batch_plan_run(pm_batch_plan *plan, void *stream);
+/* Synchronise `stream`, write each item's status and h.n, fill stats.
+ * Returns PM_OK or the first failing item's error code. */
+int pm_batch_plan_finish(pm_batch_plan *plan, pm_batch_item *items, pm_batch_stats *stats, void *stream);
+void pm_batch_plan_destroy(pm_batch_plan *plan);
+/* create + run + finish + destroy */
+int pm_batch_polymul(pm_batch_item *items, uint32_t count, const pm_batch_options *opt, pm_batch_stats *stats,
+                     void *stream);
+
 /* ---- the product without device allocation --------------------------------
  *
  * The paper has no counterpart to this entry point.  It is for callers that

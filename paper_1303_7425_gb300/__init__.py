@@ -7,6 +7,8 @@ missing.
 """
 
 from ._native import (  # noqa: F401
+    BatchPlan,
+    batch_polymul,
     PolymulError,
     Product,
     SYMBOLS,
@@ -19,4 +21,4 @@ from ._native import (  # noqa: F401
     unpack,
 )
 
-__all__ = ["polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["BatchPlan", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

@@ -63,8 +63,9 @@ class PolymulError(RuntimeError):
 
 
 # exported symbols, in include/polymul.h order
-SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_polymul_noalloc", "pm_strerror",
-           "pm_version", "pm_probe_mac")
+SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_batch_plan_create", "pm_batch_plan_run",
+           "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_polymul_noalloc",
+           "pm_strerror", "pm_version", "pm_probe_mac")
 
 _lib = None
 
@@ -261,3 +262,113 @@ def polymul_noalloc(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs,
         err.needed = int(h.n)
         raise err
     return int(h.n)
+
+
+# ---------------------------------------------------------------------------
+# batches (pm_batch_*)
+# ---------------------------------------------------------------------------
+
+BATCH_MAX_TERMS = 8192
+
+
+class pm_batch_item(C.Structure):
+    _fields_ = [("pk", pm_packing), ("coef_kind", C.c_int32), ("f", pm_terms_in), ("g", pm_terms_in),
+                ("h", pm_terms_out), ("status", C.c_int32)]
+
+
+class pm_batch_options(C.Structure):
+    _fields_ = [("range_target", C.c_uint32), ("ranges_per_item", C.c_uint32)]
+
+
+class pm_batch_stats(C.Structure):
+    _fields_ = [("term_products", C.c_uint64), ("n_out", C.c_uint64), ("n_ranges", C.c_uint64),
+                ("work_items", C.c_uint64), ("kernel_launches", C.c_uint32), ("graph", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_batch_ready = False
+
+
+def _batch_lib():
+    global _batch_ready
+    L = lib()
+    if not _batch_ready:
+        P = C.POINTER
+        L.pm_batch_plan_create.argtypes = [P(pm_batch_item), C.c_uint32, P(pm_batch_options), P(C.c_void_p),
+                                           C.c_void_p]
+        L.pm_batch_plan_create.restype = C.c_int
+        L.pm_batch_plan_run.argtypes = [C.c_void_p, C.c_void_p]
+        L.pm_batch_plan_run.restype = C.c_int
+        L.pm_batch_plan_finish.argtypes = [C.c_void_p, P(pm_batch_item), P(pm_batch_stats), C.c_void_p]
+        L.pm_batch_plan_finish.restype = C.c_int
+        L.pm_batch_plan_destroy.argtypes = [C.c_void_p]
+        L.pm_batch_plan_destroy.restype = None
+        L.pm_batch_polymul.argtypes = [P(pm_batch_item), C.c_uint32, P(pm_batch_options), P(pm_batch_stats),
+                                       C.c_void_p]
+        L.pm_batch_polymul.restype = C.c_int
+        _batch_ready = True
+    return L
+
+
+class BatchPlan:
+    """A batch of products captured once into a CUDA graph.
+
+    ``products``: list of dicts with keys field_bits, kind ('m61'/'i64'),
+    f_exps, f_coefs, g_exps, g_coefs (CUDA tensors) and out = (keys, coefs)
+    CUDA tensors (their length is the capacity).  The tensors must stay alive
+    and unmoved while the plan exists."""
+
+    def __init__(self, products, range_target: int = 0, ranges_per_item: int = 0, stream=None):
+        self.products = products
+        n = len(products)
+        self.items = (pm_batch_item * n)()
+        for k, pr in enumerate(products):
+            _check_cuda(pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], pr["out"][0], pr["out"][1])
+            it = self.items[k]
+            it.pk = packing(pr["field_bits"])
+            it.coef_kind = KIND[pr.get("kind", "m61")]
+            it.f = _terms_in(pr["f_exps"], pr["f_coefs"])
+            it.g = _terms_in(pr["g_exps"], pr["g_coefs"])
+            it.h.keys = pr["out"][0].data_ptr()
+            it.h.coefs = pr["out"][1].data_ptr()
+            it.h.cap = int(pr["out"][0].shape[0])
+        self.opt = pm_batch_options(range_target, ranges_per_item)
+        self.handle = C.c_void_p()
+        rc = _batch_lib().pm_batch_plan_create(self.items, n, C.byref(self.opt), C.byref(self.handle),
+                                               _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_batch_plan_create")
+
+    def run(self, stream=None):
+        rc = _batch_lib().pm_batch_plan_run(self.handle, _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_batch_plan_run")
+
+    def finish(self, stream=None):
+        """Returns (list of (status, n) per product, stats dict)."""
+        st = pm_batch_stats()
+        _batch_lib().pm_batch_plan_finish(self.handle, self.items, C.byref(st), _stream_handle(stream))
+        return [(int(it.status), int(it.h.n)) for it in self.items], st.as_dict()
+
+    def close(self):
+        if self.handle:
+            _batch_lib().pm_batch_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_polymul(products, range_target: int = 0, ranges_per_item: int = 0, stream=None):
+    """One-shot batch: create, run, finish, destroy."""
+    plan = BatchPlan(products, range_target, ranges_per_item, stream)
+    try:
+        plan.run(stream)
+        return plan.finish(stream)
+    finally:
+        plan.close()

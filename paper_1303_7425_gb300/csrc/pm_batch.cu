@@ -1,0 +1,921 @@
+// K-f: many independent products in one device pass (include/polymul.h,
+// pm_batch_*), captured once in a CUDA graph.
+//
+// Alg. 1 of the paper applied to every product of the batch at once, with
+// no host synchronisation between the steps:
+//   B1  one CTA per operand: pack (Sec. 7), sort, combine repeated
+//       monomials, drop zeros (the sorted distributed format of Sec. 2);
+//   B2  one CTA per product: the error rules, then the first step of
+//       Alg. 1 -- the almost regular grid of Sec. 5 over the product's
+//       pp-matrix, sorted -- gives splitters S; consecutive splitters bound
+//       left-closed, right-open ranges with about `target` term products;
+//   B3  a persistent kernel: each CTA takes work items (a run of
+//       consecutive ranges of one product) from a device counter -- the
+//       dynamic scheduling of Sec. 2 -- keeps per-row column cursors in
+//       shared memory so FindEdge for the next range is a short gallop, and
+//       sorts and reduces each range in shared memory (ranges with more
+//       products than fit are bisected by key);
+//   B4  one CTA per product concatenates its ranges in ascending order into
+//       the caller's output and reports the result size or an error.
+// No two CTAs write the same output term.  Scratch for range results is
+// claimed from a device bump counter, bounded by the products' term
+// products.
+#include <cstring>
+#include <vector>
+
+#include "pm_blocksort.cuh"
+
+namespace pm {
+
+constexpr u32 BT_MAX_TERMS = PM_BATCH_MAX_TERMS;  // per operand
+constexpr int CAN_T = 1024;                       // B1 threads
+constexpr int CAN_IPT = 8;                        // 8192 items
+constexpr int PLAN_T = 1024;                      // B2 threads
+constexpr u32 PLAN_SAMPLES = 8192;
+constexpr int RNG_T = 512;                        // B3 threads
+constexpr u32 RNG_CHUNK = 3072;                   // products sorted per piece
+constexpr int RNG_IPT = RNG_CHUNK / RNG_T;
+constexpr u32 ROWS_PER_T = BT_MAX_TERMS / RNG_T;  // 16
+constexpr int FIN_T = 512;
+
+// per-product descriptor (device); fields after `out_` are written by the
+// kernels
+struct BDesc {
+    Layout L;
+    i64 kind;
+    const u32 *fe;
+    const u64 *fc;
+    const u32 *ge;
+    const u64 *gc;
+    u64 *hkey;
+    u64 *hcoef;
+    u64 hcap;
+    u32 nf, ng;
+    u64 op_off;   // canonical f at op_off, g at op_off + nf
+    u64 rg_off;   // ranges [rg_off, rg_off + rcap)
+    u32 rcap;
+    u32 pad0;
+    // out_
+    u32 status;   // ST_* bits
+    u32 cf, cg, nranges;
+    u64 n_out;
+    u32 maxe[2][PM_MAX_VARS];
+    u64 maxabs[2];
+};
+
+struct BArgs {
+    BDesc *D;
+    u32 count;
+    u64 *ck, *cc;                 // canonical operand keys / coefficients
+    u64 *rlo, *rhi, *rbase, *rcount;
+    const u32 *item_prod, *item_first;
+    u32 nitems;
+    u32 *work;                    // work counter
+    u64 *bump;                    // output scratch counter
+    u64 *skey, *scoef;            // output scratch; coefficient words per term: cw
+    u32 cw;
+    u32 target;                   // term products per range
+    u32 per_item;                 // ranges per work item
+};
+
+// ---------------------------------------------------------------------------
+// B1: canonical operands
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(CAN_T) kb_canon(BArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u64 ws[32];
+    __shared__ u64 orv, andv;
+    __shared__ u32 maxe[PM_MAX_VARS];
+    __shared__ u64 maxabs;
+    const u32 p = blockIdx.x >> 1, side = blockIdx.x & 1, tid = threadIdx.x;
+    BDesc &d = a.D[p];
+    const u32 n = side ? d.ng : d.nf;
+    const u32 *exps = side ? d.ge : d.fe;
+    const u64 *coefs = side ? d.gc : d.fc;
+    const Layout &L = d.L;
+    const int kind = (int)d.kind;
+    u64 *kA = (u64 *)smem, *kB = kA + BT_MAX_TERMS;
+    uint16_t *iA = (uint16_t *)(kB + BT_MAX_TERMS), *iB = iA + BT_MAX_TERMS;
+    u32 *hist = (u32 *)(iB + BT_MAX_TERMS);
+    if (tid == 0) {
+        orv = 0;
+        andv = ~0ull;
+        maxabs = 0;
+    }
+    if (tid < PM_MAX_VARS) maxe[tid] = 0;
+    __syncthreads();
+    u64 o = 0, an = ~0ull;
+    u32 bad = 0;
+    for (u32 t = tid; t < n; t += CAN_T) {
+        u64 key = 0;
+        for (u32 v = 0; v < L.nv; v++) {
+            const u64 e = exps[(size_t)t * L.nv + v];
+            if (e >= (1ull << (L.width[v] - 1))) bad = 1;
+            key |= e << L.off[v];
+        }
+        kA[t] = key;
+        iA[t] = (uint16_t)t;
+        o |= key;
+        an &= key;
+    }
+    if (bad) atomicOr(&d.status, ST_EXP_OVERFLOW);
+    atomicOr(&orv, o);
+    atomicAnd(&andv, an);
+    __syncthreads();
+    int nbits = 0;
+    for (u64 x = orv ^ andv; x; x >>= 1) nbits++;
+    block_sort_pairs<CAN_T, CAN_IPT>(kA, iA, kB, iB, n, nbits, hist, ws);
+
+    // combine runs of equal keys, drop zero sums, write in order
+    u64 *ck = a.ck + d.op_off + (side ? d.nf : 0), *cc = a.cc + d.op_off + (side ? d.nf : 0);
+    u32 run = 0;
+    u64 ma = 0;
+    for (u32 t0 = 0; t0 < n; t0 += CAN_T) {
+        const u32 i = t0 + tid;
+        u64 v = 0;
+        bool nz = false;
+        if (i < n && (i == 0 || kA[i] != kA[i - 1])) {
+            if (kind == PM_COEF_M61) {
+                for (u32 j = i; j < n && kA[j] == kA[i]; j++) v = m61_add(v, m61_reduce(coefs[iA[j]]));
+                nz = v != 0;
+            } else {
+                u64 lo = 0, hi = 0;
+                for (u32 j = i; j < n && kA[j] == kA[i]; j++) {
+                    const u64 c = coefs[iA[j]];
+                    add128(lo, hi, c, (u64)((i64)c >> 63));
+                }
+                if (hi != (u64)((i64)lo >> 63)) atomicOr(&d.status, ST_COEF_BOUND);
+                v = lo;
+                nz = (lo | hi) != 0;
+                if (nz) {
+                    const u64 m = (i64)lo < 0 ? (u64)0 - lo : lo;
+                    ma = m > ma ? m : ma;
+                }
+            }
+        }
+        u64 cnt;
+        const u64 pos = block_exclusive_scan(nz ? 1 : 0, cnt, ws);
+        if (nz) {
+            ck[run + pos] = kA[i];
+            cc[run + pos] = v;
+            for (u32 vv = 0; vv < L.nv; vv++) atomicMax(&maxe[vv], key_field(L, kA[i], vv));
+        }
+        run += (u32)cnt;
+    }
+    if (kind != PM_COEF_M61) atomicMax(&maxabs, ma);
+    __syncthreads();
+    if (tid == 0) {
+        if (side) d.cg = run;
+        else d.cf = run;
+        d.maxabs[side] = maxabs;
+    }
+    if (tid < PM_MAX_VARS) d.maxe[side][tid] = maxe[tid];
+}
+
+// ---------------------------------------------------------------------------
+// B2: error rules and ranges
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(PLAN_T) kb_plan(BArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u64 ws[32];
+    __shared__ u32 flag, nuniq;
+    const u32 p = blockIdx.x, tid = threadIdx.x;
+    BDesc &d = a.D[p];
+    const Layout &L = d.L;
+    if (tid == 0) {
+        u32 st = d.status;
+        if (!st && d.cf && d.cg) {
+            for (u32 v = 0; v < L.nv; v++)
+                if ((u64)d.maxe[0][v] + d.maxe[1][v] >= (1ull << (L.width[v] - 1))) st |= ST_EXP_OVERFLOW;
+            if (d.kind != PM_COEF_M61) {
+                const unsigned __int128 m = (unsigned __int128)d.maxabs[0] * d.maxabs[1];
+                const unsigned __int128 lim = ((((unsigned __int128)1) << 127) - 1) / (d.cf < d.cg ? d.cf : d.cg);
+                if (m > lim) st |= ST_COEF_BOUND;
+            }
+        }
+        d.status = st;
+        flag = (st || !d.cf || !d.cg) ? 1u : 0u;
+        if (flag) d.nranges = 0;
+    }
+    __syncthreads();
+    if (flag) return;
+    const u32 cf = d.cf, cg = d.cg;
+    const u64 *A = a.ck + d.op_off, *B = A + d.nf;
+    const u64 lo = A[0] + B[0], end = A[cf - 1] + B[cg - 1] + 1;  // gamma_end
+    const u64 P = (u64)cf * cg;
+    u64 R = (P + a.target - 1) / a.target;
+    if (R > d.rcap) R = d.rcap;
+    if (R > PLAN_SAMPLES) R = PLAN_SAMPLES;
+    u64 *rlo = a.rlo + d.rg_off, *rhi = a.rhi + d.rg_off;
+    if (R <= 1) {
+        if (tid == 0) {
+            rlo[0] = lo;
+            rhi[0] = end;
+            d.nranges = 1;
+        }
+        return;
+    }
+    // Sec. 5 grid with about R points: steps floor(n/l) clamped to >= 1,
+    // alternate rows shifted by floor(n_b / 2l), plus the last row and column
+    // (l+1)^2 ~ R points; floor-divided steps can give more, so shrink l
+    // until the whole grid fits the sample buffer
+    u32 l = 1;
+    while ((u64)(l + 2) * (l + 2) <= R) l++;
+    u32 si, sj, Rr, Cc;
+    u64 ns64;
+    for (;;) {
+        si = cf / l ? cf / l : 1;
+        sj = cg / l ? cg / l : 1;
+        Rr = (cf + si - 1) / si;
+        Cc = (cg + sj - 1) / sj;
+        ns64 = (u64)Rr * Cc + Cc + Rr;
+        if (ns64 <= PLAN_SAMPLES || l == 1) break;
+        l--;
+    }
+    const u32 stagger = cg / (2 * l);
+    const u32 ns = (u32)(ns64 < PLAN_SAMPLES ? ns64 : PLAN_SAMPLES);
+    u64 *kA = (u64 *)smem, *kB = kA + PLAN_SAMPLES;
+    uint16_t *iA = (uint16_t *)(kB + PLAN_SAMPLES), *iB = iA + PLAN_SAMPLES;
+    u32 *hist = (u32 *)(iB + PLAN_SAMPLES);
+    for (u32 q = tid; q < ns; q += PLAN_T) {
+        u32 i, j;
+        if (q < Rr * Cc) {
+            const u32 r = q / Cc, c = q % Cc;
+            i = r * si;
+            j = (r & 1) * stagger + c * sj;
+        } else if (q < Rr * Cc + Cc) {
+            i = cf - 1;
+            j = (q - Rr * Cc) * sj;
+        } else {
+            i = (q - Rr * Cc - Cc) * si;
+            j = cg - 1;
+        }
+        if (i > cf - 1) i = cf - 1;
+        if (j > cg - 1) j = cg - 1;
+        kA[q] = A[i] + B[j];
+        iA[q] = (uint16_t)q;
+    }
+    __syncthreads();
+    block_sort_pairs<PLAN_T, PLAN_SAMPLES / PLAN_T>(kA, iA, kB, iB, ns, varying_bits(lo, end - 1), hist, ws);
+    // distinct samples strictly inside (lo, end): kB[0..nuniq)
+    u32 run = 0;
+    for (u32 t0 = 0; t0 < ns; t0 += PLAN_T) {
+        const u32 q = t0 + tid;
+        const bool keep = q < ns && kA[q] > lo && kA[q] < end && (q == 0 || kA[q] != kA[q - 1]);
+        u64 cnt;
+        const u64 pos = block_exclusive_scan(keep ? 1 : 0, cnt, ws);
+        if (keep) kB[run + pos] = kA[q];
+        run += (u32)cnt;
+    }
+    if (tid == 0) nuniq = run;
+    __syncthreads();
+    // R - 1 splitters at evenly spaced order statistics, deduplicated
+    const u32 m = nuniq;
+    const u32 want = (u32)R - 1 < m ? (u32)R - 1 : m;
+    run = 0;
+    for (u32 t0 = 0; t0 < want; t0 += PLAN_T) {
+        const u32 k = t0 + tid;
+        u64 s = 0;
+        bool keep = false;
+        if (k < want) {
+            const u32 at = (u32)(((u64)(k + 1) * m) / (want + 1));
+            s = kB[at < m ? at : m - 1];
+            const u32 atp = k ? (u32)(((u64)k * m) / (want + 1)) : 0;
+            keep = k == 0 || s != kB[atp < m ? atp : m - 1];
+        }
+        u64 cnt;
+        const u64 pos = block_exclusive_scan(keep ? 1 : 0, cnt, ws);
+        if (keep) rlo[1 + run + pos] = s;  // splitter k starts range k + 1
+        run += (u32)cnt;
+    }
+    __syncthreads();
+    const u32 nr = run + 1;
+    for (u32 k = tid; k < nr; k += PLAN_T) {
+        if (k == 0) rlo[0] = lo;
+        rhi[k] = k + 1 < nr ? rlo[k + 1] : end;
+    }
+    if (tid == 0) d.nranges = nr;
+}
+
+// ---------------------------------------------------------------------------
+// B3: ranges, persistent
+// ---------------------------------------------------------------------------
+
+// smallest j' >= j with B[j'] >= x (n if none), B sorted
+__device__ __forceinline__ u32 gallop_up(const u64 *B, u32 n, u32 j, u64 x)
+{
+    if (j >= n || B[j] >= x) return j;
+    u32 lo = j;  // B[lo] < x
+    u32 step = 1;
+    for (;;) {
+        const u32 probe = lo + step;
+        if (probe >= n || B[probe] >= x) {
+            // answer in (lo, min(probe, n)]
+            const u32 top = probe < n ? probe : n;
+            u32 a = lo + 1, len = top - a;
+            while (len > 0) {
+                const u32 half = len >> 1;
+                if (B[a + half] < x) {
+                    a += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            return a;
+        }
+        lo = probe;
+        step <<= 1;
+    }
+}
+
+struct RngSmem {
+    u64 *Bs;          // g's canonical keys
+    uint16_t *cur;    // per row: first column not yet consumed
+    u64 *kA, *kB;     // sort buffers (raw product keys)
+    uint16_t *iA, *iB;
+    u64 *cv;          // product coefficients: lo words [0, CHUNK), hi words [CHUNK, 2 CHUNK)
+    u32 *hist;
+};
+
+constexpr size_t RNG_SMEM = (size_t)BT_MAX_TERMS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
+                            (RNG_T / 32) * 256 * 4;
+
+__device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
+{
+    RngSmem m;
+    m.Bs = (u64 *)p;
+    m.kA = m.Bs + BT_MAX_TERMS;
+    m.kB = m.kA + RNG_CHUNK;
+    m.cv = m.kB + RNG_CHUNK;
+    m.hist = (u32 *)(m.cv + 2 * RNG_CHUNK);
+    m.cur = (uint16_t *)(m.hist + (RNG_T / 32) * 256);
+    m.iA = m.cur + BT_MAX_TERMS;
+    m.iB = m.iA + RNG_CHUNK;
+    return m;
+}
+
+// One piece [plo, phi) whose column edges are cur (start) and jh (end, per
+// thread's rows): generate its O <= RNG_CHUNK products, sort, reduce, and
+// write the non-zero terms at out + written.  Returns the terms written.
+__device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
+                         u32 cf, u32 r0, u32 r1, const u32 *jh, u64 plo, u64 phi, u64 out, u64 *ws)
+{
+    const u32 tid = threadIdx.x;
+    const int kind = (int)d.kind;
+    u64 mine = 0;
+    for (u32 r = r0; r < r1; r++) mine += jh[r - r0] - m.cur[r];
+    u64 O;
+    u64 base = block_exclusive_scan(mine, O, ws);
+    for (u32 r = r0; r < r1; r++) {
+        const u64 a_key = A[r], a_c = Ac[r];
+        for (u32 j = m.cur[r]; j < jh[r - r0]; j++) {
+            const u32 q = (u32)base++;
+            if (q >= RNG_CHUNK) break;  // cannot happen: O <= RNG_CHUNK here
+            m.kA[q] = a_key + m.Bs[j];
+            m.iA[q] = (uint16_t)q;
+            if (kind == PM_COEF_M61) {
+                m.cv[q] = m61_reduce(m61_mul_lazy(a_c, Bc[j]));
+            } else {
+                u64 lo, hi;
+                mul_i64_wide((i64)a_c, (i64)Bc[j], lo, hi);
+                m.cv[q] = lo;
+                m.cv[RNG_CHUNK + q] = hi;
+            }
+        }
+    }
+    __syncthreads();
+    const u32 n = (u32)(O < RNG_CHUNK ? O : RNG_CHUNK);
+    block_sort_pairs<RNG_T, RNG_IPT>(m.kA, m.iA, m.kB, m.iB, n, varying_bits(plo, phi - 1), m.hist, ws);
+    u64 run = 0;
+    for (u32 t0 = 0; t0 < n; t0 += RNG_T) {
+        const u32 i = t0 + tid;
+        u64 v0 = 0, v1 = 0;
+        bool nz = false;
+        if (i < n && (i == 0 || m.kA[i] != m.kA[i - 1])) {
+            for (u32 j = i; j < n && m.kA[j] == m.kA[i]; j++) {
+                const u32 s = m.iA[j];
+                if (kind == PM_COEF_M61) v0 = m61_add(v0, m.cv[s]);
+                else add128(v0, v1, m.cv[s], m.cv[RNG_CHUNK + s]);
+            }
+            nz = (v0 | v1) != 0;
+        }
+        u64 cnt;
+        const u64 pos = block_exclusive_scan(nz ? 1 : 0, cnt, ws);
+        if (nz) {
+            const u64 dst = out + run + pos;
+            a.skey[dst] = m.kA[i];
+            a.scoef[a.cw * dst] = v0;
+            if (a.cw == 2) a.scoef[2 * dst + 1] = v1;
+        }
+        run += cnt;
+    }
+    __syncthreads();
+    return run;
+}
+
+// sum of all products of a single-monomial piece with more than RNG_CHUNK
+// products; writes at most one term
+__device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
+                          u32 r0, u32 r1, const u32 *jh, u64 key, u64 out, u64 *ws)
+{
+    const int kind = (int)d.kind;
+    u64 s0 = 0, s1 = 0;
+    for (u32 r = r0; r < r1; r++)
+        for (u32 j = m.cur[r]; j < jh[r - r0]; j++) {
+            if (kind == PM_COEF_M61) {
+                s0 = m61_add(s0, m61_reduce(m61_mul_lazy(Ac[r], Bc[j])));
+            } else {
+                u64 lo, hi;
+                mul_i64_wide((i64)Ac[r], (i64)Bc[j], lo, hi);
+                add128(s0, s1, lo, hi);
+            }
+        }
+    // block reduction through the scan helper, word by word with carries
+    __shared__ u64 red[2 * (RNG_T / 32)];
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int dd = 16; dd > 0; dd >>= 1) {
+        const u64 o0 = __shfl_down_sync(0xffffffffu, s0, dd), o1 = __shfl_down_sync(0xffffffffu, s1, dd);
+        if (kind == PM_COEF_M61) s0 = m61_add(s0, o0);
+        else add128(s0, s1, o0, o1);
+    }
+    if (lane == 0) {
+        red[2 * w] = s0;
+        red[2 * w + 1] = s1;
+    }
+    __syncthreads();
+    __shared__ u64 wrote;
+    if (threadIdx.x == 0) {
+        u64 r0w = 0, r1w = 0;
+        for (int ww = 0; ww < RNG_T / 32; ww++) {
+            if (kind == PM_COEF_M61) r0w = m61_add(r0w, red[2 * ww]);
+            else add128(r0w, r1w, red[2 * ww], red[2 * ww + 1]);
+        }
+        wrote = 0;
+        if ((r0w | r1w) != 0) {
+            a.skey[out] = key;
+            a.scoef[a.cw * out] = r0w;
+            if (a.cw == 2) a.scoef[2 * out + 1] = r1w;
+            wrote = 1;
+        }
+    }
+    __syncthreads();
+    return wrote;
+}
+
+__global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u64 ws[32];
+    __shared__ u32 item;
+    __shared__ u64 claim;
+    RngSmem m = carve_rng(smem);
+    const u32 tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) item = atomicAdd(a.work, 1u);
+        __syncthreads();
+        const u32 it = item;
+        __syncthreads();
+        if (it >= a.nitems) break;
+        const u32 p = a.item_prod[it], first = a.item_first[it];
+        const BDesc &d = a.D[p];
+        if (d.status || first >= d.nranges) continue;
+        const u32 last = min(first + a.per_item, d.nranges);
+        const u32 cf = d.cf, cg = d.cg;
+        const u64 *A = a.ck + d.op_off, *Ac = a.cc + d.op_off;
+        const u64 *Bg = A + d.nf, *Bc = Ac + d.nf;
+        for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
+        __syncthreads();
+        // rows of this thread: [r0, r1); cursors at the first range's start
+        const u32 r0 = min(tid * ROWS_PER_T, cf), r1 = min(r0 + ROWS_PER_T, cf);
+        u32 jh[ROWS_PER_T];
+        {
+            const u64 lo = a.rlo[d.rg_off + first];
+            for (u32 r = r0; r < r1; r++) {
+                const u64 ar = A[r];
+                u32 c = 0;
+                if (lo > ar) {
+                    const u64 x = lo - ar;
+                    u32 lo2 = 0, len = cg;
+                    while (len > 0) {
+                        const u32 half = len >> 1;
+                        if (m.Bs[lo2 + half] < x) {
+                            lo2 += half + 1;
+                            len -= half + 1;
+                        } else {
+                            len = half;
+                        }
+                    }
+                    c = lo2;
+                }
+                m.cur[r] = (uint16_t)c;
+            }
+        }
+        __syncthreads();
+        for (u32 k = first; k < last; k++) {
+            const u64 rlo_k = a.rlo[d.rg_off + k], rhi_k = a.rhi[d.rg_off + k];
+            // edges at the range end and the range's product count
+            u64 mine = 0;
+            for (u32 r = r0; r < r1; r++) {
+                const u64 ar = A[r];
+                const u32 e = rhi_k > ar ? gallop_up(m.Bs, cg, m.cur[r], rhi_k - ar) : m.cur[r];
+                jh[r - r0] = e;
+                mine += e - m.cur[r];
+            }
+            u64 O;
+            block_exclusive_scan(mine, O, ws);
+            // claim the range's output space (at most O terms)
+            if (tid == 0) claim = atomicAdd(a.bump, O);
+            __syncthreads();
+            const u64 out = claim;
+            u64 written = 0;
+            if (O <= RNG_CHUNK) {
+                if (O) written = rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, rlo_k, rhi_k, out, ws);
+                for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
+                __syncthreads();
+            } else {
+                // bisect by key: pieces [plo, phi) with at most RNG_CHUNK
+                // products, or a single monomial
+                u64 plo = rlo_k;
+                while (plo < rhi_k) {
+                    u64 phi = rhi_k;
+                    for (;;) {
+                        u64 cnt_mine = 0;
+                        for (u32 r = r0; r < r1; r++) {
+                            const u64 ar = A[r];
+                            const u32 e = phi > ar ? gallop_up(m.Bs, cg, m.cur[r], phi - ar) : m.cur[r];
+                            jh[r - r0] = e;
+                            cnt_mine += e - m.cur[r];
+                        }
+                        u64 PO;
+                        block_exclusive_scan(cnt_mine, PO, ws);
+                        if (PO <= RNG_CHUNK) {
+                            if (PO) written += rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, plo, phi, out + written, ws);
+                            break;
+                        }
+                        if (phi - plo == 1) {
+                            written += rng_single(a, d, m, A, Ac, Bc, r0, r1, jh, plo, out + written, ws);
+                            break;
+                        }
+                        phi = plo + (phi - plo) / 2;
+                    }
+                    for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
+                    __syncthreads();
+                    plo = phi;
+                }
+            }
+            if (tid == 0) {
+                a.rbase[d.rg_off + k] = out;
+                a.rcount[d.rg_off + k] = written;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// B4: concatenate each product's ranges into its output
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
+{
+    __shared__ u64 ws[32];
+    __shared__ u64 fo[FIN_T];
+    const u32 p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    BDesc &d = a.D[p];
+    if (d.status) {
+        if (tid == 0) d.n_out = 0;
+        return;
+    }
+    const u32 nr = d.nranges;
+    const u64 *rb = a.rbase + d.rg_off, *rc = a.rcount + d.rg_off;
+    u64 total = 0;
+    for (u32 k0 = 0; k0 < nr; k0 += FIN_T) {
+        const u32 k = k0 + tid;
+        u64 cnt;
+        block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
+        total += cnt;
+    }
+    if (total > d.hcap) {
+        if (tid == 0) {
+            d.n_out = total;
+            d.status |= ST_CAPACITY;
+        }
+        return;
+    }
+    u64 run = 0;
+    for (u32 k0 = 0; k0 < nr; k0 += FIN_T) {
+        const u32 k = k0 + tid;
+        u64 cnt;
+        fo[tid] = run + block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
+        __syncthreads();
+        // warp w copies ranges k0 + w, k0 + w + 16, ...
+        for (u32 q = w; q < FIN_T && k0 + q < nr; q += FIN_T / 32) {
+            const u64 src = rb[k0 + q], dst = fo[q], n = rc[k0 + q];
+            for (u64 t = lane; t < n; t += 32) {
+                d.hkey[dst + t] = a.skey[src + t];
+                if (d.kind == PM_COEF_M61) {
+                    d.hcoef[dst + t] = a.scoef[a.cw * (src + t)];
+                } else {
+                    d.hcoef[2 * (dst + t)] = a.scoef[2 * (src + t)];
+                    d.hcoef[2 * (dst + t) + 1] = a.scoef[2 * (src + t) + 1];
+                }
+            }
+        }
+        run += cnt;
+        __syncthreads();
+    }
+    if (tid == 0) d.n_out = total;
+}
+
+// ---------------------------------------------------------------------------
+// host: plan, graph, run, finish
+// ---------------------------------------------------------------------------
+
+template <class K>
+static void set_smem_b(K kernel, size_t bytes)
+{
+    PM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+constexpr size_t CAN_SMEM = (size_t)BT_MAX_TERMS * (8 + 8 + 2 + 2) + (CAN_T / 32) * 256 * 4;
+constexpr size_t PLAN_SMEM = (size_t)PLAN_SAMPLES * (8 + 8 + 2 + 2) + (PLAN_T / 32) * 256 * 4;
+
+}  // namespace pm
+
+struct pm_batch_plan {
+    int device = 0;
+    uint32_t count = 0;
+    pm::BArgs args;
+    pm::BDesc *d_desc = nullptr;
+    std::vector<pm::BDesc> h_desc;
+    std::vector<void *> blocks;   // device allocations owned by the plan
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    pm_batch_stats stats;
+    int sm_count = 148;
+};
+
+namespace pm {
+
+static void *plan_alloc(pm_batch_plan *pl, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes < 256) bytes = 256;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error(PM_ENOMEM, "batch plan allocation failed");
+    }
+    pl->blocks.push_back(p);
+    return p;
+}
+
+static void plan_enqueue(pm_batch_plan *pl, cudaStream_t s)
+{
+    const BArgs &a = pl->args;
+    PM_CUDA(cudaMemsetAsync(a.work, 0, sizeof(u32), s));
+    PM_CUDA(cudaMemsetAsync(a.bump, 0, sizeof(u64), s));
+    kb_canon<<<2 * pl->count, CAN_T, CAN_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_plan<<<pl->count, PLAN_T, PLAN_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_ranges<<<pl->sm_count, RNG_T, RNG_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_finish<<<pl->count, FIN_T, 0, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+}
+
+static void batch_create(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                         pm_batch_plan *pl, cudaStream_t stream)
+{
+    if (!items || count == 0) throw Error(PM_EINVAL, "empty batch");
+    pm_batch_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    const u32 target = o.range_target ? o.range_target : 1536;
+    const u32 per_item = o.ranges_per_item ? o.ranges_per_item : 16;
+    if (target < 64 || target > RNG_CHUNK || per_item < 1 || per_item > 4096) throw Error(PM_EINVAL, "bad batch options");
+    PM_CUDA(cudaGetDevice(&pl->device));
+    PM_CUDA(cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device));
+    pl->count = count;
+    pl->h_desc.resize(count);
+    u64 op_total = 0, rg_total = 0, prod_total = 0;
+    bool wide = false;
+    std::vector<u32> item_prod, item_first;
+    for (u32 p = 0; p < count; p++) {
+        const pm_batch_item &it = items[p];
+        const pm_packing &pk = it.pk;
+        if (pk.nvars < 1 || pk.nvars > PM_MAX_VARS) throw Error(PM_EINVAL, "bad nvars");
+        if (it.coef_kind != PM_COEF_M61 && it.coef_kind != PM_COEF_I64_ACC128) throw Error(PM_EINVAL, "bad kind");
+        if (it.f.n > BT_MAX_TERMS || it.g.n > BT_MAX_TERMS) throw Error(PM_EINVAL, "operand above PM_BATCH_MAX_TERMS");
+        if ((it.f.n && (!it.f.exps || !it.f.coefs)) || (it.g.n && (!it.g.exps || !it.g.coefs)))
+            throw Error(PM_EINVAL, "null operand arrays");
+        if (it.h.cap && (!it.h.keys || !it.h.coefs)) throw Error(PM_EINVAL, "null output arrays");
+        BDesc &d = pl->h_desc[p];
+        memset(&d, 0, sizeof(d));
+        d.L.nv = pk.nvars;
+        u32 s = 0;
+        for (int v = (int)pk.nvars - 1; v >= 0; v--) {
+            if (pk.field_bits[v] < 1 || pk.field_bits[v] > 32) throw Error(PM_EINVAL, "bad field width");
+            d.L.off[v] = s;
+            d.L.width[v] = pk.field_bits[v];
+            s += pk.field_bits[v];
+        }
+        if (s > 64) throw Error(PM_EINVAL, "fields exceed 64 bits");
+        d.kind = it.coef_kind;
+        wide |= it.coef_kind == PM_COEF_I64_ACC128;
+        d.fe = it.f.exps;
+        d.fc = (const u64 *)it.f.coefs;
+        d.nf = (u32)it.f.n;
+        d.ge = it.g.exps;
+        d.gc = (const u64 *)it.g.coefs;
+        d.ng = (u32)it.g.n;
+        d.hkey = (u64 *)it.h.keys;
+        d.hcoef = (u64 *)it.h.coefs;
+        d.hcap = it.h.cap;
+        d.op_off = op_total;
+        op_total += d.nf + d.ng;
+        const u64 P = (u64)d.nf * d.ng;
+        prod_total += P;
+        u64 rcap = P ? (P + target - 1) / target + 1 : 1;
+        if (rcap > PLAN_SAMPLES) rcap = PLAN_SAMPLES;
+        d.rcap = (u32)rcap;
+        d.rg_off = rg_total;
+        rg_total += rcap;
+        for (u32 f0 = 0; f0 < rcap; f0 += per_item) {
+            item_prod.push_back(p);
+            item_first.push_back(f0);
+        }
+    }
+    BArgs &a = pl->args;
+    memset(&a, 0, sizeof(a));
+    a.count = count;
+    a.cw = wide ? 2 : 1;
+    a.target = target;
+    a.per_item = per_item;
+    a.nitems = (u32)item_prod.size();
+    pl->d_desc = (BDesc *)plan_alloc(pl, sizeof(BDesc) * count);
+    a.D = pl->d_desc;
+    a.ck = (u64 *)plan_alloc(pl, 8 * (op_total + 1));
+    a.cc = (u64 *)plan_alloc(pl, 8 * (op_total + 1));
+    a.rlo = (u64 *)plan_alloc(pl, 8 * rg_total);
+    a.rhi = (u64 *)plan_alloc(pl, 8 * rg_total);
+    a.rbase = (u64 *)plan_alloc(pl, 8 * rg_total);
+    a.rcount = (u64 *)plan_alloc(pl, 8 * rg_total);
+    u32 *ip = (u32 *)plan_alloc(pl, 4 * item_prod.size());
+    u32 *ifr = (u32 *)plan_alloc(pl, 4 * item_first.size());
+    a.item_prod = ip;
+    a.item_first = ifr;
+    a.work = (u32 *)plan_alloc(pl, 8);
+    a.bump = (u64 *)plan_alloc(pl, 8);
+    a.skey = (u64 *)plan_alloc(pl, 8 * (prod_total + 1));
+    a.scoef = (u64 *)plan_alloc(pl, 8 * a.cw * (prod_total + 1));
+    PM_CUDA(cudaMemcpyAsync(ip, item_prod.data(), 4 * item_prod.size(), cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaMemcpyAsync(ifr, item_first.data(), 4 * item_first.size(), cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaMemcpyAsync(pl->d_desc, pl->h_desc.data(), sizeof(BDesc) * count, cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaStreamSynchronize(stream));
+    memset(&pl->stats, 0, sizeof(pl->stats));
+    pl->stats.term_products = prod_total;
+    pl->stats.work_items = a.nitems;
+    pl->stats.kernel_launches = 4;
+
+    set_smem_b(kb_canon, CAN_SMEM);
+    set_smem_b(kb_plan, PLAN_SMEM);
+    set_smem_b(kb_ranges, RNG_SMEM);
+    // capture the whole pass once; runs replay it
+    cudaStream_t cs;
+    PM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        try {
+            plan_enqueue(pl, cs);
+        } catch (...) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            throw;
+        }
+        e = cudaStreamEndCapture(cs, &pl->graph);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) throw Error(PM_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    PM_CUDA(cudaGraphInstantiate(&pl->exec, pl->graph, 0));
+    pl->stats.graph = 1;
+}
+
+static void batch_destroy(pm_batch_plan *pl)
+{
+    if (!pl) return;
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    for (void *p : pl->blocks) cudaFree(p);
+    pl->blocks.clear();
+}
+
+static int batch_finish(pm_batch_plan *pl, pm_batch_item *items, pm_batch_stats *st, cudaStream_t s)
+{
+    PM_CUDA(cudaMemcpyAsync(pl->h_desc.data(), pl->d_desc, sizeof(BDesc) * pl->count, cudaMemcpyDeviceToHost, s));
+    PM_CUDA(cudaStreamSynchronize(s));
+    int worst = PM_OK;
+    u64 n_out = 0, ranges = 0;
+    for (u32 p = 0; p < pl->count; p++) {
+        const BDesc &d = pl->h_desc[p];
+        int rc = PM_OK;
+        if (d.status & ST_EXP_OVERFLOW) rc = PM_EEXP_OVERFLOW;
+        else if (d.status & ST_COEF_BOUND) rc = PM_ECOEF_BOUND;
+        else if (d.status & ST_CAPACITY) rc = PM_ECAPACITY;
+        else if (d.status) rc = PM_ECUDA;
+        if (items) {
+            items[p].status = rc;
+            items[p].h.n = (rc == PM_OK || rc == PM_ECAPACITY) ? d.n_out : 0;
+        }
+        if (rc == PM_OK) n_out += d.n_out;
+        ranges += d.nranges;
+        if (rc != PM_OK && worst == PM_OK) worst = rc;
+    }
+    pl->stats.n_out = n_out;
+    pl->stats.n_ranges = ranges;
+    if (st) *st = pl->stats;
+    return worst;
+}
+
+}  // namespace pm
+
+// ---------------------------------------------------------------------------
+// C-ABI
+// ---------------------------------------------------------------------------
+
+template <class F>
+static int bguard(F &&fn)
+{
+    try {
+        return fn();
+    } catch (const pm::Error &e) {
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return PM_ENOMEM;
+    } catch (...) {
+        return PM_ECUDA;
+    }
+}
+
+extern "C" int pm_batch_plan_create(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                                    pm_batch_plan **plan, void *stream)
+{
+    if (!plan) return PM_EINVAL;
+    *plan = nullptr;
+    pm_batch_plan *pl = new (std::nothrow) pm_batch_plan();
+    if (!pl) return PM_ENOMEM;
+    int rc = bguard([&] {
+        pm::batch_create(items, count, opt, pl, (cudaStream_t)stream);
+        return PM_OK;
+    });
+    if (rc != PM_OK) {
+        pm::batch_destroy(pl);
+        delete pl;
+        return rc;
+    }
+    *plan = pl;
+    return PM_OK;
+}
+
+extern "C" int pm_batch_plan_run(pm_batch_plan *plan, void *stream)
+{
+    if (!plan || !plan->exec) return PM_EINVAL;
+    return bguard([&] {
+        PM_CUDA(cudaGraphLaunch(plan->exec, (cudaStream_t)stream));
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_batch_plan_finish(pm_batch_plan *plan, pm_batch_item *items, pm_batch_stats *stats, void *stream)
+{
+    if (!plan) return PM_EINVAL;
+    return bguard([&] { return pm::batch_finish(plan, items, stats, (cudaStream_t)stream); });
+}
+
+extern "C" void pm_batch_plan_destroy(pm_batch_plan *plan)
+{
+    if (!plan) return;
+    pm::batch_destroy(plan);
+    delete plan;
+}
+
+extern "C" int pm_batch_polymul(pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                                pm_batch_stats *stats, void *stream)
+{
+    pm_batch_plan *pl = nullptr;
+    int rc = pm_batch_plan_create(items, count, opt, &pl, stream);
+    if (rc != PM_OK) return rc;
+    rc = pm_batch_plan_run(pl, stream);
+    if (rc == PM_OK) rc = pm_batch_plan_finish(pl, items, stats, stream);
+    pm_batch_plan_destroy(pl);
+    return rc;
+}

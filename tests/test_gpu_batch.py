@@ -1,0 +1,136 @@
+"""The batched pass (pm_batch_*): every product of a mixed batch equals the
+oracle and equals the same product computed alone by pm_polymul (bit-exact),
+errors stay per item, and replaying the captured graph recomputes from the
+current inputs."""
+
+import numpy as np
+import pytest
+
+import oracle
+import polygen
+from tests.gpu_util import pack_np, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _product(w, cap=None):
+    import torch
+    f = to_dev(w.f.exps, w.f.coefs, w.kind)
+    g = to_dev(w.g.exps, w.g.coefs, w.kind)
+    cap = cap if cap is not None else max(w.f.n * w.g.n, 1)
+    words = 1 if w.kind == "m61" else 2
+    out = (torch.full((cap,), -1, dtype=torch.int64, device="cuda"),
+           torch.full((cap, words) if words == 2 else (cap,), -1, dtype=torch.int64, device="cuda"))
+    return dict(field_bits=w.field_bits, kind=w.kind, f_exps=f[0], f_coefs=f[1], g_exps=g[0], g_coefs=g[1],
+                out=out, w=w)
+
+
+def _mixed_workloads(seed=5, count=40):
+    st = polygen.Stream(seed, 0)
+    ws = []
+    nv = 3 + st.below(6, count).astype(int)
+    nf = polygen.log_uniform_size(st, count, 16, 1200)
+    ng = polygen.log_uniform_size(st, count, 16, 1200)
+    for k in range(count):
+        ws.append(polygen.sparse_product(polygen.Stream(seed, 100 + k), int(nv[k]), int(nf[k]), int(ng[k])))
+    # dense small products (many products per monomial)
+    mons = polygen.monomials_total_degree(3, 8)
+    s2 = polygen.Stream(seed, 999)
+    ws.append(polygen.Workload("dense3", 3, [10] * 3, "m61", polygen.Poly(mons, s2.coef_m61(len(mons))),
+                               polygen.Poly(mons[::-1].copy(), s2.coef_m61(len(mons)))))
+    # int64 kind with repeated monomials
+    e = s2.below(4, 300 * 3).astype(np.uint32).reshape(300, 3)
+    ws.append(polygen.Workload("i64rep", 3, [8] * 3, "i64", polygen.Poly(e, s2.coef_i64(300, 1 << 30)),
+                               polygen.Poly(e[::-1].copy(), s2.coef_i64(300, 1 << 30))))
+    return ws
+
+
+def _check_against_oracle(pr, n):
+    w = pr["w"]
+    e, c = oracle.mul(w.nvars, w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    assert n == len(e)
+    keys = pr["out"][0][:n].cpu().numpy().view(np.uint64)
+    coefs = pr["out"][1][:n].cpu().numpy().view(np.uint64)
+    np.testing.assert_array_equal(keys, pack_np(e, w.field_bits))
+    np.testing.assert_array_equal(coefs.reshape(-1), np.asarray(c, dtype=np.uint64).reshape(-1))
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(range_target=64, ranges_per_item=1), dict(range_target=3072,
+                                                                                          ranges_per_item=64)])
+def test_batch_matches_oracle_and_single(opts):
+    import paper_1303_7425_gb300 as P
+    prods = [_product(w) for w in _mixed_workloads()]
+    res, stats = P.batch_polymul(prods, **opts)
+    assert stats["graph"] == 1
+    for pr, (status, n) in zip(prods, res):
+        assert status == 0
+        _check_against_oracle(pr, n)
+        single = P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], kind=pr["kind"])
+        assert single.n == n
+        np.testing.assert_array_equal(single.keys.cpu().numpy(), pr["out"][0][:n].cpu().numpy())
+        np.testing.assert_array_equal(single.coefs.cpu().numpy(), pr["out"][1][:n].cpu().numpy())
+
+
+def test_batch_errors_stay_per_item():
+    import paper_1303_7425_gb300 as P
+    ws = _mixed_workloads(count=6)
+    prods = [_product(w) for w in ws]
+    one = np.array([1], np.uint64)
+    bad = polygen.Workload("ovf", 2, [4, 4], "m61", polygen.Poly(np.array([[4, 0]], np.uint32), one),
+                           polygen.Poly(np.array([[4, 1]], np.uint32), one))
+    small = _product(ws[0], cap=3)
+    zero = polygen.Workload("zero", 2, [8, 8], "m61", polygen.Poly(np.array([[1, 1], [2, 2]], np.uint32),
+                                                                   np.array([0, 0], np.uint64)),
+                            polygen.Poly(np.array([[1, 0]], np.uint32), one))
+    prods = prods[:3] + [_product(bad), small, _product(zero)] + prods[3:]
+    res, _ = P.batch_polymul(prods)
+    for k, (pr, (status, n)) in enumerate(zip(prods, res)):
+        if k == 3:
+            assert status == -2
+        elif k == 4:
+            assert status == -4 and n > 3
+        elif k == 5:
+            assert status == 0 and n == 0
+        else:
+            assert status == 0
+            _check_against_oracle(pr, n)
+
+
+def test_batch_heavy_multiplicity():
+    """Univariate dense operands: up to 3500 products per monomial, so ranges
+    above the shared-memory chunk are bisected and single monomials summed."""
+    import paper_1303_7425_gb300 as P
+    st = polygen.Stream(31, 0)
+    e = np.arange(3500, dtype=np.uint32).reshape(-1, 1)
+    w = polygen.Workload("uni", 1, [16], "m61", polygen.Poly(e, st.coef_m61(3500)),
+                         polygen.Poly(e[::-1].copy(), st.coef_m61(3500)))
+    prods = [_product(w, cap=7000)]
+    res, stats = P.batch_polymul(prods)
+    assert res[0][0] == 0
+    _check_against_oracle(prods[0], res[0][1])
+
+
+def test_graph_replay_recomputes_from_inputs():
+    import paper_1303_7425_gb300 as P
+    ws = _mixed_workloads(seed=9, count=12)
+    prods = [_product(w) for w in ws]
+    plan = P.BatchPlan(prods)
+    try:
+        plan.run()
+        res1, _ = plan.finish()
+        for pr, (status, n) in zip(prods, res1):
+            assert status == 0
+            _check_against_oracle(pr, n)
+        # change product 0's coefficients in place and replay
+        w0 = ws[0]
+        new = polygen.Stream(123, 0).coef_m61(w0.f.n)
+        prods[0]["f_coefs"].copy_(to_dev(w0.f.exps, new)[1])
+        w0.f.coefs = new
+        plan.run()
+        plan.run()
+        res2, _ = plan.finish()
+        for pr, (status, n) in zip(prods, res2):
+            assert status == 0
+            _check_against_oracle(pr, n)
+    finally:
+        plan.close()
