@@ -213,6 +213,70 @@ void pm_batch_plan_destroy(pm_batch_plan *plan);
 int pm_batch_polymul(pm_batch_item *items, uint32_t count, const pm_batch_options *opt, pm_batch_stats *stats,
                      void *stream);
 
+/* Workspace mode of the same pass, for engines that own their memory and
+ * streams: nothing is allocated and nothing synchronises, so it can also be
+ * captured into a graph by the caller.  pm_batch_workspace reports the
+ * device bytes (256-byte aligned workspace) and pinned host bytes the items
+ * need; pm_batch_enqueue puts the pass on `stream`, copying the items'
+ * descriptors from host_ws and their results back into host_ws at the end;
+ * once the stream has passed that point, pm_batch_collect writes each item's
+ * status and h.n from host_ws.  The workspaces must not be reused before
+ * then. */
+int pm_batch_workspace(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                       uint64_t *device_bytes, uint64_t *host_bytes);
+int pm_batch_enqueue(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt, void *device_ws,
+                     uint64_t device_bytes, void *host_ws, uint64_t host_bytes, void *stream);
+int pm_batch_collect(pm_batch_item *items, uint32_t count, const void *host_ws);
+
+/* ---- serving: a continuous-batching request loop ----------------------------
+ *
+ * The paper has no serving layer; this is the request loop the library adds
+ * around the batched pass.  Requests (one product each, with device-resident
+ * inputs and outputs owned by the caller) are admitted in arrival order
+ * whenever one of `streams` stream slots and enough of the engine's device
+ * arena (`device_budget` bytes, the HBM budget, allocated once at create)
+ * and pinned staging are free; the admitted products that fit the batch
+ * kernels form one batch (at most `max_batch`), enqueued in workspace mode,
+ * so batches admitted while others run overlap on the device.  Products
+ * above PM_BATCH_MAX_TERMS go to a worker thread running pm_polymul on its
+ * own stream.  A request whose workspace can never fit the budget completes
+ * with PM_ENOMEM.  All calls on one server must come from one host thread. */
+typedef struct pm_server pm_server;
+
+typedef struct pm_server_config {
+    uint64_t device_budget;    /* device arena bytes (default 8 GiB)              */
+    uint64_t host_budget;      /* pinned staging bytes (default 64 MiB)           */
+    uint32_t streams;          /* batches in flight at most (default 4)           */
+    uint32_t max_batch;        /* products per batch at most (default 256)        */
+    pm_batch_options batch;
+} pm_server_config;
+
+typedef struct pm_server_done {
+    uint64_t tag;              /* the caller's tag from pm_server_submit          */
+    int32_t status;            /* PM_OK or the product's error code               */
+    uint32_t pad;
+    uint64_t n;                /* result terms written to the request's h          */
+    double t_submit, t_admit, t_done;  /* server clock, seconds                   */
+} pm_server_done;
+
+typedef struct pm_server_state_t {
+    uint32_t queued, in_flight, big_queued, big_active, max_in_flight, pad;
+    uint64_t batches;          /* batches launched so far                         */
+    uint64_t device_used;      /* arena bytes held by batches in flight           */
+    double clock;              /* server clock, seconds                           */
+} pm_server_state_t;
+
+int pm_server_create(const pm_server_config *cfg, pm_server **srv);
+/* Queue one product (the descriptor is copied; the device buffers it points
+ * to must stay valid until the request completes). */
+int pm_server_submit(pm_server *srv, const pm_batch_item *item, uint64_t tag);
+/* Reap finished batches, admit and launch queued requests, and return up to
+ * `cap` completions.  Never blocks on the device. */
+int pm_server_progress(pm_server *srv, pm_server_done *done, uint32_t cap, uint32_t *n_done);
+int pm_server_state(pm_server *srv, pm_server_state_t *state);
+/* Waits for work in flight, then frees the server's memory and streams. */
+void pm_server_destroy(pm_server *srv);
+
 /* ---- the product without device allocation --------------------------------
  *
  * The paper has no counterpart to this entry point.  It is for callers that

@@ -8,6 +8,7 @@ missing.
 
 from ._native import (  # noqa: F401
     BatchPlan,
+    Server,
     batch_polymul,
     PolymulError,
     Product,
@@ -21,4 +22,4 @@ from ._native import (  # noqa: F401
     unpack,
 )
 
-__all__ = ["BatchPlan", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["BatchPlan", "Server", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

@@ -64,7 +64,9 @@ class PolymulError(RuntimeError):
 
 # exported symbols, in include/polymul.h order
 SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_batch_plan_create", "pm_batch_plan_run",
-           "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_polymul_noalloc",
+           "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_batch_workspace",
+           "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_progress",
+           "pm_server_state", "pm_server_destroy", "pm_polymul_noalloc",
            "pm_strerror", "pm_version", "pm_probe_mac")
 
 _lib = None
@@ -372,3 +374,105 @@ def batch_polymul(products, range_target: int = 0, ranges_per_item: int = 0, str
         return plan.finish(stream)
     finally:
         plan.close()
+
+
+# ---------------------------------------------------------------------------
+# serving engine (pm_server_*)
+# ---------------------------------------------------------------------------
+
+class pm_server_config(C.Structure):
+    _fields_ = [("device_budget", C.c_uint64), ("host_budget", C.c_uint64), ("streams", C.c_uint32),
+                ("max_batch", C.c_uint32), ("batch", pm_batch_options)]
+
+
+class pm_server_done(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("status", C.c_int32), ("pad", C.c_uint32), ("n", C.c_uint64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double)]
+
+
+class pm_server_state_t(C.Structure):
+    _fields_ = [("queued", C.c_uint32), ("in_flight", C.c_uint32), ("big_queued", C.c_uint32),
+                ("big_active", C.c_uint32), ("max_in_flight", C.c_uint32), ("pad", C.c_uint32),
+                ("batches", C.c_uint64), ("device_used", C.c_uint64), ("clock", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_server_ready = False
+
+
+def _server_lib():
+    global _server_ready
+    L = _batch_lib()
+    if not _server_ready:
+        P = C.POINTER
+        L.pm_server_create.argtypes = [P(pm_server_config), P(C.c_void_p)]
+        L.pm_server_create.restype = C.c_int
+        L.pm_server_submit.argtypes = [C.c_void_p, P(pm_batch_item), C.c_uint64]
+        L.pm_server_submit.restype = C.c_int
+        L.pm_server_progress.argtypes = [C.c_void_p, P(pm_server_done), C.c_uint32, P(C.c_uint32)]
+        L.pm_server_progress.restype = C.c_int
+        L.pm_server_state.argtypes = [C.c_void_p, P(pm_server_state_t)]
+        L.pm_server_state.restype = C.c_int
+        L.pm_server_destroy.argtypes = [C.c_void_p]
+        L.pm_server_destroy.restype = None
+        _server_ready = True
+    return L
+
+
+def _batch_item(pr) -> pm_batch_item:
+    _check_cuda(pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], pr["out"][0], pr["out"][1])
+    it = pm_batch_item()
+    it.pk = packing(pr["field_bits"])
+    it.coef_kind = KIND[pr.get("kind", "m61")]
+    it.f = _terms_in(pr["f_exps"], pr["f_coefs"])
+    it.g = _terms_in(pr["g_exps"], pr["g_coefs"])
+    it.h.keys = pr["out"][0].data_ptr()
+    it.h.coefs = pr["out"][1].data_ptr()
+    it.h.cap = int(pr["out"][0].shape[0])
+    return it
+
+
+class Server:
+    """The native continuous-batching engine (pm_server_*)."""
+
+    def __init__(self, device_budget: int = 0, host_budget: int = 0, streams: int = 0, max_batch: int = 0,
+                 range_target: int = 0, ranges_per_item: int = 0):
+        cfg = pm_server_config(device_budget, host_budget, streams, max_batch,
+                               pm_batch_options(range_target, ranges_per_item))
+        self.handle = C.c_void_p()
+        rc = _server_lib().pm_server_create(C.byref(cfg), C.byref(self.handle))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_server_create")
+        self._buf = (pm_server_done * 4096)()
+
+    def submit(self, product, tag: int):
+        it = _batch_item(product)
+        rc = _server_lib().pm_server_submit(self.handle, C.byref(it), tag)
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_server_submit")
+
+    def progress(self):
+        n = C.c_uint32()
+        rc = _server_lib().pm_server_progress(self.handle, self._buf, len(self._buf), C.byref(n))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_server_progress")
+        return [dict(tag=int(d.tag), status=int(d.status), n=int(d.n), t_submit=d.t_submit, t_admit=d.t_admit,
+                     t_done=d.t_done) for d in self._buf[:n.value]]
+
+    def state(self):
+        st = pm_server_state_t()
+        _server_lib().pm_server_state(self.handle, C.byref(st))
+        return st.as_dict()
+
+    def close(self):
+        if self.handle:
+            _server_lib().pm_server_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -21,6 +21,7 @@
 // claimed from a device bump counter, bounded by the products' term
 // products.
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "pm_blocksort.cuh"
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
 }
 
 // ---------------------------------------------------------------------------
-// host: plan, graph, run, finish
+// host: layout, enqueue, plans (graph), workspace mode
 // ---------------------------------------------------------------------------
 
 template <class K>
@@ -646,68 +647,61 @@ static void set_smem_b(K kernel, size_t bytes)
 constexpr size_t CAN_SMEM = (size_t)BT_MAX_TERMS * (8 + 8 + 2 + 2) + (CAN_T / 32) * 256 * 4;
 constexpr size_t PLAN_SMEM = (size_t)PLAN_SAMPLES * (8 + 8 + 2 + 2) + (PLAN_T / 32) * 256 * 4;
 
-}  // namespace pm
-
-struct pm_batch_plan {
-    int device = 0;
-    uint32_t count = 0;
-    pm::BArgs args;
-    pm::BDesc *d_desc = nullptr;
-    std::vector<pm::BDesc> h_desc;
-    std::vector<void *> blocks;   // device allocations owned by the plan
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    pm_batch_stats stats;
-    int sm_count = 148;
+struct BatchSizes {
+    u64 op_total = 0, rg_total = 0, prod_total = 0;
+    u32 nitems = 0, cw = 1, target = 0, per_item = 0;
 };
 
-namespace pm {
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-static void *plan_alloc(pm_batch_plan *pl, size_t bytes)
-{
-    void *p = nullptr;
-    if (bytes < 256) bytes = 256;
-    cudaError_t e = cudaMalloc(&p, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        throw Error(PM_ENOMEM, "batch plan allocation failed");
+// device workspace layout (every region 256-byte aligned)
+struct WsLayout {
+    size_t D, ck, cc, rlo, rhi, rbase, rcount, ip, ifr, work, bump, skey, scoef, total;
+    WsLayout(u32 count, const BatchSizes &z)
+    {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            size_t at = o;
+            o += align256(bytes ? bytes : 8);
+            return at;
+        };
+        D = take(sizeof(BDesc) * count);
+        ck = take(8 * (z.op_total + 1));
+        cc = take(8 * (z.op_total + 1));
+        rlo = take(8 * z.rg_total);
+        rhi = take(8 * z.rg_total);
+        rbase = take(8 * z.rg_total);
+        rcount = take(8 * z.rg_total);
+        ip = take(4 * (size_t)z.nitems);
+        ifr = take(4 * (size_t)z.nitems);
+        work = take(8);
+        bump = take(8);
+        skey = take(8 * (z.prod_total + 1));
+        scoef = take(8 * (size_t)z.cw * (z.prod_total + 1));
+        total = o;
     }
-    pl->blocks.push_back(p);
-    return p;
-}
+};
 
-static void plan_enqueue(pm_batch_plan *pl, cudaStream_t s)
+// host staging layout: descriptors, then the two work-item tables
+static size_t stage_bytes(u32 count, const BatchSizes &z)
 {
-    const BArgs &a = pl->args;
-    PM_CUDA(cudaMemsetAsync(a.work, 0, sizeof(u32), s));
-    PM_CUDA(cudaMemsetAsync(a.bump, 0, sizeof(u64), s));
-    kb_canon<<<2 * pl->count, CAN_T, CAN_SMEM, s>>>(a);
-    PM_CUDA(cudaGetLastError());
-    kb_plan<<<pl->count, PLAN_T, PLAN_SMEM, s>>>(a);
-    PM_CUDA(cudaGetLastError());
-    kb_ranges<<<pl->sm_count, RNG_T, RNG_SMEM, s>>>(a);
-    PM_CUDA(cudaGetLastError());
-    kb_finish<<<pl->count, FIN_T, 0, s>>>(a);
-    PM_CUDA(cudaGetLastError());
+    return sizeof(BDesc) * count + 8 * (size_t)z.nitems;
 }
 
-static void batch_create(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
-                         pm_batch_plan *pl, cudaStream_t stream)
+// Validate the items; with descs/ip/ifr non-null also write the descriptors
+// and the work-item tables.
+static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_batch_options *opt, BDesc *descs,
+                              u32 *ip, u32 *ifr)
 {
     if (!items || count == 0) throw Error(PM_EINVAL, "empty batch");
     pm_batch_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    const u32 target = o.range_target ? o.range_target : 1536;
-    const u32 per_item = o.ranges_per_item ? o.ranges_per_item : 16;
-    if (target < 64 || target > RNG_CHUNK || per_item < 1 || per_item > 4096) throw Error(PM_EINVAL, "bad batch options");
-    PM_CUDA(cudaGetDevice(&pl->device));
-    PM_CUDA(cudaDeviceGetAttribute(&pl->sm_count, cudaDevAttrMultiProcessorCount, pl->device));
-    pl->count = count;
-    pl->h_desc.resize(count);
-    u64 op_total = 0, rg_total = 0, prod_total = 0;
-    bool wide = false;
-    std::vector<u32> item_prod, item_first;
+    BatchSizes z;
+    z.target = o.range_target ? o.range_target : 1536;
+    z.per_item = o.ranges_per_item ? o.ranges_per_item : 16;
+    if (z.target < 64 || z.target > RNG_CHUNK || z.per_item < 1 || z.per_item > 4096)
+        throw Error(PM_EINVAL, "bad batch options");
     for (u32 p = 0; p < count; p++) {
         const pm_batch_item &it = items[p];
         const pm_packing &pk = it.pk;
@@ -717,19 +711,19 @@ static void batch_create(const pm_batch_item *items, uint32_t count, const pm_ba
         if ((it.f.n && (!it.f.exps || !it.f.coefs)) || (it.g.n && (!it.g.exps || !it.g.coefs)))
             throw Error(PM_EINVAL, "null operand arrays");
         if (it.h.cap && (!it.h.keys || !it.h.coefs)) throw Error(PM_EINVAL, "null output arrays");
-        BDesc &d = pl->h_desc[p];
+        BDesc d;
         memset(&d, 0, sizeof(d));
         d.L.nv = pk.nvars;
-        u32 s = 0;
+        u32 sbits = 0;
         for (int v = (int)pk.nvars - 1; v >= 0; v--) {
             if (pk.field_bits[v] < 1 || pk.field_bits[v] > 32) throw Error(PM_EINVAL, "bad field width");
-            d.L.off[v] = s;
+            d.L.off[v] = sbits;
             d.L.width[v] = pk.field_bits[v];
-            s += pk.field_bits[v];
+            sbits += pk.field_bits[v];
         }
-        if (s > 64) throw Error(PM_EINVAL, "fields exceed 64 bits");
+        if (sbits > 64) throw Error(PM_EINVAL, "fields exceed 64 bits");
         d.kind = it.coef_kind;
-        wide |= it.coef_kind == PM_COEF_I64_ACC128;
+        if (it.coef_kind == PM_COEF_I64_ACC128) z.cw = 2;
         d.fe = it.f.exps;
         d.fc = (const u64 *)it.f.coefs;
         d.nf = (u32)it.f.n;
@@ -739,64 +733,163 @@ static void batch_create(const pm_batch_item *items, uint32_t count, const pm_ba
         d.hkey = (u64 *)it.h.keys;
         d.hcoef = (u64 *)it.h.coefs;
         d.hcap = it.h.cap;
-        d.op_off = op_total;
-        op_total += d.nf + d.ng;
+        d.op_off = z.op_total;
+        z.op_total += d.nf + d.ng;
         const u64 P = (u64)d.nf * d.ng;
-        prod_total += P;
-        u64 rcap = P ? (P + target - 1) / target + 1 : 1;
+        z.prod_total += P;
+        u64 rcap = P ? (P + z.target - 1) / z.target + 1 : 1;
         if (rcap > PLAN_SAMPLES) rcap = PLAN_SAMPLES;
         d.rcap = (u32)rcap;
-        d.rg_off = rg_total;
-        rg_total += rcap;
-        for (u32 f0 = 0; f0 < rcap; f0 += per_item) {
-            item_prod.push_back(p);
-            item_first.push_back(f0);
+        d.rg_off = z.rg_total;
+        z.rg_total += rcap;
+        for (u32 f0 = 0; f0 < rcap; f0 += z.per_item) {
+            if (ip) {
+                ip[z.nitems] = p;
+                ifr[z.nitems] = f0;
+            }
+            z.nitems++;
         }
+        if (descs) descs[p] = d;
     }
-    BArgs &a = pl->args;
-    memset(&a, 0, sizeof(a));
-    a.count = count;
-    a.cw = wide ? 2 : 1;
-    a.target = target;
-    a.per_item = per_item;
-    a.nitems = (u32)item_prod.size();
-    pl->d_desc = (BDesc *)plan_alloc(pl, sizeof(BDesc) * count);
-    a.D = pl->d_desc;
-    a.ck = (u64 *)plan_alloc(pl, 8 * (op_total + 1));
-    a.cc = (u64 *)plan_alloc(pl, 8 * (op_total + 1));
-    a.rlo = (u64 *)plan_alloc(pl, 8 * rg_total);
-    a.rhi = (u64 *)plan_alloc(pl, 8 * rg_total);
-    a.rbase = (u64 *)plan_alloc(pl, 8 * rg_total);
-    a.rcount = (u64 *)plan_alloc(pl, 8 * rg_total);
-    u32 *ip = (u32 *)plan_alloc(pl, 4 * item_prod.size());
-    u32 *ifr = (u32 *)plan_alloc(pl, 4 * item_first.size());
-    a.item_prod = ip;
-    a.item_first = ifr;
-    a.work = (u32 *)plan_alloc(pl, 8);
-    a.bump = (u64 *)plan_alloc(pl, 8);
-    a.skey = (u64 *)plan_alloc(pl, 8 * (prod_total + 1));
-    a.scoef = (u64 *)plan_alloc(pl, 8 * a.cw * (prod_total + 1));
-    PM_CUDA(cudaMemcpyAsync(ip, item_prod.data(), 4 * item_prod.size(), cudaMemcpyHostToDevice, stream));
-    PM_CUDA(cudaMemcpyAsync(ifr, item_first.data(), 4 * item_first.size(), cudaMemcpyHostToDevice, stream));
-    PM_CUDA(cudaMemcpyAsync(pl->d_desc, pl->h_desc.data(), sizeof(BDesc) * count, cudaMemcpyHostToDevice, stream));
-    PM_CUDA(cudaStreamSynchronize(stream));
-    memset(&pl->stats, 0, sizeof(pl->stats));
-    pl->stats.term_products = prod_total;
-    pl->stats.work_items = a.nitems;
-    pl->stats.kernel_launches = 4;
+    return z;
+}
 
+static BArgs carve_ws(unsigned char *base, u32 count, const BatchSizes &z)
+{
+    WsLayout w(count, z);
+    BArgs a;
+    memset(&a, 0, sizeof(a));
+    a.D = (BDesc *)(base + w.D);
+    a.count = count;
+    a.ck = (u64 *)(base + w.ck);
+    a.cc = (u64 *)(base + w.cc);
+    a.rlo = (u64 *)(base + w.rlo);
+    a.rhi = (u64 *)(base + w.rhi);
+    a.rbase = (u64 *)(base + w.rbase);
+    a.rcount = (u64 *)(base + w.rcount);
+    a.item_prod = (const u32 *)(base + w.ip);
+    a.item_first = (const u32 *)(base + w.ifr);
+    a.nitems = z.nitems;
+    a.work = (u32 *)(base + w.work);
+    a.bump = (u64 *)(base + w.bump);
+    a.skey = (u64 *)(base + w.skey);
+    a.scoef = (u64 *)(base + w.scoef);
+    a.cw = z.cw;
+    a.target = z.target;
+    a.per_item = z.per_item;
+    return a;
+}
+
+static void set_batch_smem()
+{
     set_smem_b(kb_canon, CAN_SMEM);
     set_smem_b(kb_plan, PLAN_SMEM);
     set_smem_b(kb_ranges, RNG_SMEM);
+}
+
+// the four kernels of the pass (counters cleared first)
+static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
+{
+    PM_CUDA(cudaMemsetAsync(a.work, 0, sizeof(u32), s));
+    PM_CUDA(cudaMemsetAsync(a.bump, 0, sizeof(u64), s));
+    kb_canon<<<2 * a.count, CAN_T, CAN_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_plan<<<a.count, PLAN_T, PLAN_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_ranges<<<sm_count, RNG_T, RNG_SMEM, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_finish<<<a.count, FIN_T, 0, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+}
+
+static int item_code(u32 status)
+{
+    if (status & ST_EXP_OVERFLOW) return PM_EEXP_OVERFLOW;
+    if (status & ST_COEF_BOUND) return PM_ECOEF_BOUND;
+    if (status & ST_CAPACITY) return PM_ECAPACITY;
+    if (status) return PM_ECUDA;
+    return PM_OK;
+}
+
+// write statuses and sizes from result descriptors; returns the first error
+static int collect(const BDesc *descs, u32 count, pm_batch_item *items, uint64_t *n_out, uint64_t *ranges)
+{
+    int worst = PM_OK;
+    u64 no = 0, nr = 0;
+    for (u32 p = 0; p < count; p++) {
+        const int rc = item_code(descs[p].status);
+        if (items) {
+            items[p].status = rc;
+            items[p].h.n = (rc == PM_OK || rc == PM_ECAPACITY) ? descs[p].n_out : 0;
+        }
+        if (rc == PM_OK) no += descs[p].n_out;
+        nr += descs[p].nranges;
+        if (rc != PM_OK && worst == PM_OK) worst = rc;
+    }
+    if (n_out) *n_out = no;
+    if (ranges) *ranges = nr;
+    return worst;
+}
+
+static int device_sms()
+{
+    int dev = 0, sms = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    return sms;
+}
+
+}  // namespace pm
+
+struct pm_batch_plan {
+    uint32_t count = 0;
+    pm::BArgs args;
+    pm::BatchSizes sizes;
+    std::vector<pm::BDesc> h_desc;
+    void *dws = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    pm_batch_stats stats;
+};
+
+namespace pm {
+
+static void batch_create(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                         pm_batch_plan *pl, cudaStream_t stream)
+{
+    BatchSizes z = build_batch(items, count, opt, nullptr, nullptr, nullptr);
+    pl->count = count;
+    pl->sizes = z;
+    pl->h_desc.resize(count);
+    std::vector<u32> ip(z.nitems), ifr(z.nitems);
+    build_batch(items, count, opt, pl->h_desc.data(), ip.data(), ifr.data());
+    WsLayout w(count, z);
+    if (cudaMalloc(&pl->dws, w.total) != cudaSuccess) {
+        cudaGetLastError();
+        pl->dws = nullptr;
+        throw Error(PM_ENOMEM, "batch plan allocation failed");
+    }
+    unsigned char *base = (unsigned char *)pl->dws;
+    pl->args = carve_ws(base, count, z);
+    PM_CUDA(cudaMemcpyAsync(base + w.D, pl->h_desc.data(), sizeof(BDesc) * count, cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaMemcpyAsync(base + w.ip, ip.data(), 4 * (size_t)z.nitems, cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaMemcpyAsync(base + w.ifr, ifr.data(), 4 * (size_t)z.nitems, cudaMemcpyHostToDevice, stream));
+    PM_CUDA(cudaStreamSynchronize(stream));
+    memset(&pl->stats, 0, sizeof(pl->stats));
+    pl->stats.term_products = z.prod_total;
+    pl->stats.work_items = z.nitems;
+    pl->stats.kernel_launches = 4;
+    set_batch_smem();
+    const int sms = device_sms();
     // capture the whole pass once; runs replay it
     cudaStream_t cs;
     PM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         try {
-            plan_enqueue(pl, cs);
+            launch_pass(pl->args, sms, cs);
         } catch (...) {
-            cudaGraph_t g;
+            cudaGraph_t g = nullptr;
             cudaStreamEndCapture(cs, &g);
             if (g) cudaGraphDestroy(g);
             cudaStreamDestroy(cs);
@@ -815,36 +908,56 @@ static void batch_destroy(pm_batch_plan *pl)
     if (!pl) return;
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
-    for (void *p : pl->blocks) cudaFree(p);
-    pl->blocks.clear();
+    if (pl->dws) cudaFree(pl->dws);
+    pl->exec = nullptr;
+    pl->graph = nullptr;
+    pl->dws = nullptr;
 }
 
 static int batch_finish(pm_batch_plan *pl, pm_batch_item *items, pm_batch_stats *st, cudaStream_t s)
 {
-    PM_CUDA(cudaMemcpyAsync(pl->h_desc.data(), pl->d_desc, sizeof(BDesc) * pl->count, cudaMemcpyDeviceToHost, s));
+    PM_CUDA(cudaMemcpyAsync(pl->h_desc.data(), pl->args.D, sizeof(BDesc) * pl->count, cudaMemcpyDeviceToHost, s));
     PM_CUDA(cudaStreamSynchronize(s));
-    int worst = PM_OK;
-    u64 n_out = 0, ranges = 0;
-    for (u32 p = 0; p < pl->count; p++) {
-        const BDesc &d = pl->h_desc[p];
-        int rc = PM_OK;
-        if (d.status & ST_EXP_OVERFLOW) rc = PM_EEXP_OVERFLOW;
-        else if (d.status & ST_COEF_BOUND) rc = PM_ECOEF_BOUND;
-        else if (d.status & ST_CAPACITY) rc = PM_ECAPACITY;
-        else if (d.status) rc = PM_ECUDA;
-        if (items) {
-            items[p].status = rc;
-            items[p].h.n = (rc == PM_OK || rc == PM_ECAPACITY) ? d.n_out : 0;
-        }
-        if (rc == PM_OK) n_out += d.n_out;
-        ranges += d.nranges;
-        if (rc != PM_OK && worst == PM_OK) worst = rc;
-    }
-    pl->stats.n_out = n_out;
-    pl->stats.n_ranges = ranges;
+    const int worst = collect(pl->h_desc.data(), pl->count, items, &pl->stats.n_out, &pl->stats.n_ranges);
     if (st) *st = pl->stats;
     return worst;
 }
+
+// workspace mode: everything stream-ordered, nothing allocated
+void batch_enqueue_ws(const pm_batch_item *items, u32 count, const pm_batch_options *opt, void *dws, u64 dbytes,
+                      void *hws, u64 hbytes, int sm_count, cudaStream_t s)
+{
+    const BatchSizes z = build_batch(items, count, opt, nullptr, nullptr, nullptr);
+    const WsLayout w(count, z);
+    if (!dws || dbytes < w.total || !hws || hbytes < stage_bytes(count, z))
+        throw Error(PM_EINVAL, "batch workspace too small");
+    if ((uintptr_t)dws & 255) throw Error(PM_EINVAL, "device workspace must be 256-byte aligned");
+    unsigned char *h = (unsigned char *)hws, *base = (unsigned char *)dws;
+    BDesc *descs = (BDesc *)h;
+    u32 *ip = (u32 *)(h + sizeof(BDesc) * count), *ifr = ip + z.nitems;
+    build_batch(items, count, opt, descs, ip, ifr);
+    const BArgs a = carve_ws(base, count, z);
+    PM_CUDA(cudaMemcpyAsync(base + w.D, descs, sizeof(BDesc) * count, cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(base + w.ip, ip, 4 * (size_t)z.nitems, cudaMemcpyHostToDevice, s));
+    PM_CUDA(cudaMemcpyAsync(base + w.ifr, ifr, 4 * (size_t)z.nitems, cudaMemcpyHostToDevice, s));
+    launch_pass(a, sm_count, s);
+    PM_CUDA(cudaMemcpyAsync(descs, base + w.D, sizeof(BDesc) * count, cudaMemcpyDeviceToHost, s));
+}
+
+void batch_ws_sizes(const pm_batch_item *items, u32 count, const pm_batch_options *opt, u64 *dbytes, u64 *hbytes)
+{
+    const BatchSizes z = build_batch(items, count, opt, nullptr, nullptr, nullptr);
+    const WsLayout w(count, z);
+    *dbytes = w.total;
+    *hbytes = stage_bytes(count, z);
+}
+
+int batch_collect_ws(pm_batch_item *items, u32 count, const void *hws)
+{
+    return collect((const BDesc *)hws, count, items, nullptr, nullptr);
+}
+
+void batch_prepare_device() { set_batch_smem(); }
 
 }  // namespace pm
 
@@ -918,4 +1031,36 @@ extern "C" int pm_batch_polymul(pm_batch_item *items, uint32_t count, const pm_b
     if (rc == PM_OK) rc = pm_batch_plan_finish(pl, items, stats, stream);
     pm_batch_plan_destroy(pl);
     return rc;
+}
+
+extern "C" int pm_batch_workspace(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                                  uint64_t *device_bytes, uint64_t *host_bytes)
+{
+    if (!device_bytes || !host_bytes) return PM_EINVAL;
+    return bguard([&] {
+        pm::batch_ws_sizes(items, count, opt, (pm::u64 *)device_bytes, (pm::u64 *)host_bytes);
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_batch_enqueue(const pm_batch_item *items, uint32_t count, const pm_batch_options *opt,
+                                void *device_ws, uint64_t device_bytes, void *host_ws, uint64_t host_bytes,
+                                void *stream)
+{
+    return bguard([&] {
+        static std::once_flag once;
+        std::call_once(once, [] { pm::batch_prepare_device(); });
+        int dev = 0, sms = 0;
+        PM_CUDA(cudaGetDevice(&dev));
+        PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        pm::batch_enqueue_ws(items, count, opt, device_ws, device_bytes, host_ws, host_bytes, sms,
+                             (cudaStream_t)stream);
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_batch_collect(pm_batch_item *items, uint32_t count, const void *host_ws)
+{
+    if (!items || !host_ws) return PM_EINVAL;
+    return pm::batch_collect_ws(items, count, host_ws);
 }

@@ -1,0 +1,85 @@
+"""The serving engine: Poisson arrivals, continuous batching over several
+streams, HBM-budget admission.  Each result must be the same in the mix as
+alone (bit-exact, the tolerance of every test here), and equal the oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+import polygen
+from tests.gpu_util import pack_np, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _prod(w):
+    import torch
+    f = to_dev(w.f.exps, w.f.coefs, w.kind)
+    g = to_dev(w.g.exps, w.g.coefs, w.kind)
+    cap = max(w.f.n * w.g.n, 1)
+    if w.f.n > 8192 or w.g.n > 8192:          # dense products: their box bounds the result
+        cap = 200_000
+    out = (torch.full((cap,), -1, dtype=torch.int64, device="cuda"),
+           torch.full((cap,), -1, dtype=torch.int64, device="cuda"))
+    return dict(field_bits=w.field_bits, kind=w.kind, f_exps=f[0], f_coefs=f[1], g_exps=g[0], g_coefs=g[1],
+                out=out)
+
+
+def _stream(count=150, dense=3, seed=17, rate=20000.0, hi=800):
+    st = polygen.Stream(seed, 0)
+    nv = 3 + st.below(6, count).astype(int)
+    nf = polygen.log_uniform_size(st, count, 16, hi)
+    ng = polygen.log_uniform_size(st, count, 16, hi)
+    ws = [polygen.sparse_product(polygen.Stream(seed, 10 + k), int(nv[k]), int(nf[k]), int(ng[k]))
+          for k in range(count)]
+    for k in range(dense):
+        ws.insert(10 + 40 * k, polygen.workload_c2(seed=seed + k))
+    gaps = -np.log(1.0 - st.uniform01(len(ws))) / rate
+    return ws, np.cumsum(gaps)
+
+
+def test_serving_results_equal_alone_and_oracle():
+    import paper_1303_7425_gb300 as P
+    from paper_1303_7425_gb300.serving import serve
+    ws, t = _stream()
+    prods = [_prod(w) for w in ws]
+    rep = serve(list(zip(t.tolist(), prods)), [w.term_products for w in ws],
+                server_kwargs=dict(streams=4, max_batch=16, device_budget=4 << 30))
+    assert rep["failed"] == 0
+    assert rep["state"]["max_in_flight"] >= 2          # batches overlapped on the device
+    assert rep["p99_ms"] >= rep["p50_ms"] > 0
+    for k, (w, pr) in enumerate(zip(ws, prods)):
+        n = rep["done"][k]["n"]
+        alone = P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"])
+        assert alone.n == n
+        np.testing.assert_array_equal(alone.keys.cpu().numpy(), pr["out"][0][:n].cpu().numpy())
+        np.testing.assert_array_equal(alone.coefs.cpu().numpy(), pr["out"][1][:n].cpu().numpy())
+    rng = np.random.default_rng(1)
+    sparse = [k for k, w in enumerate(ws) if w.f.n <= 8192]
+    for k in rng.choice(sparse, size=15, replace=False):
+        w = ws[k]
+        e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+        n = rep["done"][k]["n"]
+        np.testing.assert_array_equal(prods[k]["out"][0][:n].cpu().numpy().view(np.uint64), pack_np(e, w.field_bits))
+        np.testing.assert_array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)
+
+
+def test_serving_budget_admission():
+    from paper_1303_7425_gb300.serving import serve
+    ws, t = _stream(count=40, dense=0, seed=23, rate=1e6, hi=400)
+    huge = polygen.sparse_product(polygen.Stream(99, 0), 4, 4096, 4096)     # 16.7M products
+    ws.append(huge)
+    t = np.append(t, t[-1])
+    prods = [_prod(w) for w in ws]
+    # 8 MiB of arena: every small product fits alone (<= 160,000 products),
+    # the stream as a whole does not, and the huge request never fits
+    rep = serve(list(zip(t.tolist(), prods)), [w.term_products for w in ws],
+                server_kwargs=dict(streams=2, max_batch=64, device_budget=8 << 20))
+    assert rep["done"][len(ws) - 1]["status"] == -5
+    assert all(rep["done"][k]["status"] == 0 for k in range(len(ws) - 1))
+    assert rep["state"]["batches"] > 2                 # admission split the stream into several batches
+    for k in range(0, len(ws) - 1, 7):
+        w = ws[k]
+        e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+        n = rep["done"][k]["n"]
+        np.testing.assert_array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)
