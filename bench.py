@@ -49,6 +49,11 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
+                    help="what the timed steps run (profiling); the reported line is for c2")
+    ap.add_argument("--c4-count", type=int, default=4096, help="products of the batched workload")
+    ap.add_argument("--c5-count", type=int, default=3000, help="requests of the serving workload")
     return ap.parse_args()
 
 
@@ -250,6 +255,113 @@ def e2e_product(P, torch, w, steps, warmup):
     return times, h2d, d2h
 
 
+def _device_product(torch, np, w, cap=None):
+    f = (torch.from_numpy(w.f.exps.view(np.int32).copy()).cuda(), torch.from_numpy(w.f.coefs.view(np.int64).copy()).cuda())
+    g = (torch.from_numpy(w.g.exps.view(np.int32).copy()).cuda(), torch.from_numpy(w.g.coefs.view(np.int64).copy()).cuda())
+    cap = cap if cap is not None else max(w.f.n * w.g.n, 1)
+    out = (torch.empty(cap, dtype=torch.int64, device="cuda"), torch.empty(cap, dtype=torch.int64, device="cuda"))
+    return dict(field_bits=w.field_bits, kind=w.kind, f_exps=f[0], f_coefs=f[1], g_exps=g[0], g_coefs=g[1], out=out)
+
+
+def bench_batched(P, torch, count, tune=True):
+    """c4: `count` independent sparse products -- one captured batched pass
+    versus one pm_polymul launch per product, on the same GPU."""
+    import numpy as np
+
+    import oracle
+    import polygen
+    ws = polygen.workload_c4(count)
+    prods = [_device_product(torch, np, w) for w in ws]
+    tp = sum(w.term_products for w in ws)
+    best = P.batch_autotune(prods)[0] if tune else {}
+    plan = P.BatchPlan(prods, **best)
+    plan.run()
+    res, st = plan.finish()
+    times = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        plan.run()
+        b.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    res, st = plan.finish()
+    plan.close()
+    failed = sum(1 for s_, _ in res if s_ != 0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for pr in prods:
+        P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], out=pr["out"])
+    b.record()
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b)
+    # parity of the batched results on sampled products
+    plan = P.BatchPlan(prods, **best)
+    plan.run()
+    res, _ = plan.finish()
+    plan.close()
+    rng = np.random.default_rng(0)
+    small = [k for k, w in enumerate(ws) if w.term_products <= 1_000_000]
+    checked = 0
+    for k in rng.choice(small, size=min(8, len(small)), replace=False):
+        w = ws[k]
+        e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+        n = res[k][1]
+        ok = n == len(e) and np.array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)
+        checked += 1 if ok else 0
+    ms = statistics.mean(times)
+    del prods
+    torch.cuda.empty_cache()
+    return {"products": count, "term_products": tp, "batched_ms": ms, "batched_value": tp / (ms * 1e-3),
+            "plain_ms": plain_ms, "plain_value": tp / (plain_ms * 1e-3), "batched_vs_plain_speedup": plain_ms / ms,
+            "unit": UNIT, "options": best, "ranges": st["n_ranges"], "work_items": st["work_items"],
+            "graph": bool(st["graph"]), "failed": failed, "oracle_checked": checked,
+            "oracle_sampled": int(min(8, len(small)))}
+
+
+def bench_serving(P, torch, count, rate_hz, tune=True):
+    """c5: Poisson arrivals at `rate_hz`, 95% c4-distribution and 5% dense
+    c2-shape products, continuous batching under a 64 GiB HBM budget."""
+    import numpy as np
+
+    import oracle
+    import polygen
+    from paper_1303_7425_gb300.serving import serve
+    reqs = polygen.workload_c5(rate_hz, count)
+    prods = [_device_product(torch, np, r.work, cap=(200_000 if r.dense else None)) for r in reqs]
+    rep = serve([(r.t_arrival, pr) for r, pr in zip(reqs, prods)], [r.work.term_products for r in reqs],
+                server_kwargs=dict(device_budget=64 << 30, streams=4, max_batch=256))
+    # every result equals the same product computed alone
+    same = 0
+    for k, (r, pr) in enumerate(zip(reqs, prods)):
+        n = rep["done"][k]["n"]
+        if r.dense:
+            alone = P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"])
+            ok = alone.n == n and torch.equal(alone.coefs, pr["out"][1][:n]) and torch.equal(alone.keys, pr["out"][0][:n])
+        else:
+            cap = max(r.work.f.n * r.work.g.n, 1)
+            out = (torch.empty(cap, dtype=torch.int64, device="cuda"), torch.empty(cap, dtype=torch.int64, device="cuda"))
+            alone = P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], out=out)
+            ok = alone.n == n and torch.equal(alone.coefs, pr["out"][1][:n]) and torch.equal(alone.keys, pr["out"][0][:n])
+        same += 1 if ok else 0
+    rng = np.random.default_rng(1)
+    small = [k for k, r in enumerate(reqs) if not r.dense and r.work.term_products <= 500_000]
+    checked = 0
+    for k in rng.choice(small, size=min(8, len(small)), replace=False):
+        w = reqs[k].work
+        e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+        n = rep["done"][k]["n"]
+        checked += 1 if (n == len(e) and np.array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)) else 0
+    del prods
+    torch.cuda.empty_cache()
+    return {"requests": count, "rate_hz": rate_hz, "dense_requests": int(sum(r.dense for r in reqs)),
+            "p50_ms": rep["p50_ms"], "p99_ms": rep["p99_ms"], "mean_ms": rep["mean_ms"],
+            "value": rep["term_products_per_s"], "unit": UNIT, "failed": rep["failed"],
+            "same_alone_and_in_mix": same, "oracle_checked": checked, "oracle_sampled": int(min(8, len(small))),
+            "batches": rep["state"]["batches"], "max_batches_in_flight": rep["state"]["max_in_flight"],
+            "hbm_budget_gib": 64}
+
+
 def cpu_baseline(w):
     import oracle
     t0 = time.perf_counter()
@@ -286,9 +398,17 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.lib()  # fails loudly if the CUDA library is missing
 
-    w = polygen.workload_c2()
+    w = {"c2": polygen.workload_c2, "c3": polygen.workload_c3}.get(args.workload, polygen.workload_c2)()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     products = w.term_products
+    if args.workload == "c4":  # profiling aid: the batched pass as the timed step
+        print(json.dumps(bench_batched(P, torch, args.c4_count, tune=not args.no_tune)))
+        return
+    tuned = None
+    if not args.no_tune:
+        f = _dev(torch, np, w.f)
+        g = _dev(torch, np, w.g)
+        tuned = P.autotune(w.field_bits, f[0], f[1], g[0], g[1])[0]
 
     # warm-up (also fills the stream-ordered allocator's pool)
     time_product(P, torch, w, 1, args.warmup, flush)
@@ -333,12 +453,21 @@ def run_ours(args):
                                          "ms_per_step": statistics.mean(ms_i),
                                          "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_i)}
             w3 = polygen.workload_c3()
+            if not args.no_tune:
+                f3 = _dev(torch, np, w3.f)
+                g3 = _dev(torch, np, w3.g)
+                P.autotune(w3.field_bits, f3[0], f3[1], g3[0], g3[1])
             ms_3, st_3, r3 = time_product(P, torch, w3, 5, 2, flush)
             extras["c3_sparse5v_50000x50000"] = {
                 "value": w3.term_products / (statistics.mean(ms_3) * 1e-3), "unit": UNIT,
                 "ms_per_step": statistics.mean(ms_3), "n_out": r3.n,
                 "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_3),
                 "kernel_frac_of_probe": w3.term_products / (statistics.mean(s["ms_range_kernel"] for s in st_3) * 1e-3) / peak}
+            c4 = bench_batched(P, torch, args.c4_count, tune=not args.no_tune)
+            extras["c4_batched"] = c4
+            # serving at ~70% of the measured batched capacity (products per second)
+            rate = 0.7 * args.c4_count / (c4["batched_ms"] * 1e-3)
+            extras["c5_serving"] = bench_serving(P, torch, args.c5_count, rate, tune=not args.no_tune)
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(w)
         if cpu is not None:
             extras["cpu_alg1_threads"] = cpu_alg1(w)
@@ -346,8 +475,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 mod 2^61-1", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "flushed between timed steps (256 MiB write, outside the events)",
-                       "strategy": stats[-1]["strategy"], "ranges": stats[-1]["n_ranges"],
+            "config": {"workload": WORKLOAD if args.workload == "c2" else args.workload,
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "strategy": stats[-1]["strategy"], "ranges": stats[-1]["n_ranges"], "tuned": tuned,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof,
             "cpu_baseline": {k: v for k, v in cpu.items() if k != "n_out"} if cpu else None,

@@ -157,6 +157,30 @@ int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *
  * Fails with PM_EEXP_OVERFLOW if an exponent reaches its guard bit. */
 int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream);
 
+/* ---- autotuning ---------------------------------------------------------------
+ *
+ * Like the paper's one-time tuning of l (Sec. 5, Sec. 7), but over this
+ * library's knobs: pm_autotune runs every candidate configuration (direct
+ * strategy x groups per SM x window slots x accumulator, sort strategy x
+ * chunk) on the given product, times each with CUDA events on `stream`,
+ * returns the fastest in *best and keeps it for the product's shape class
+ * (kind, nvars, floor(log2) of n_f, n_g and of pm_out_bound's value);
+ * pm_polymul called with NULL or all-zero options uses the kept choice for
+ * products of that class.  h receives the product.  pm_batch_autotune does
+ * the same for a batch's range size and ranges per work item, timing plans
+ * on an evenly spaced sample of at most 256 items. */
+#define PM_TUNE_MAX_CANDIDATES 16
+
+typedef struct pm_tune_report {
+    uint32_t count;            /* candidates timed                                */
+    uint32_t best;             /* index of the fastest                            */
+    pm_options candidates[PM_TUNE_MAX_CANDIDATES];
+    float ms[PM_TUNE_MAX_CANDIDATES];  /* best of 2 runs; -1 when refused         */
+} pm_tune_report;
+
+int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g, pm_terms_out *h,
+                pm_options *best, pm_tune_report *report, void *stream);
+
 /* ---- batches of independent products (one device pass, a CUDA graph) ------
  *
  * Alg. 1 applied to every product of a batch in one pass: per operand,
@@ -212,6 +236,15 @@ void pm_batch_plan_destroy(pm_batch_plan *plan);
 /* create + run + finish + destroy */
 int pm_batch_polymul(pm_batch_item *items, uint32_t count, const pm_batch_options *opt, pm_batch_stats *stats,
                      void *stream);
+
+typedef struct pm_batch_tune_report {
+    uint32_t count, best, sample;
+    pm_batch_options candidates[PM_TUNE_MAX_CANDIDATES];
+    float ms[PM_TUNE_MAX_CANDIDATES];
+} pm_batch_tune_report;
+
+int pm_batch_autotune(const pm_batch_item *items, uint32_t count, pm_batch_options *best,
+                      pm_batch_tune_report *report, void *stream);
 
 /* Workspace mode of the same pass, for engines that own their memory and
  * streams: nothing is allocated and nothing synchronises, so it can also be

@@ -63,7 +63,8 @@ class PolymulError(RuntimeError):
 
 
 # exported symbols, in include/polymul.h order
-SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_batch_plan_create", "pm_batch_plan_run",
+SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_autotune", "pm_batch_autotune",
+           "pm_batch_plan_create", "pm_batch_plan_run",
            "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_batch_workspace",
            "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_progress",
            "pm_server_state", "pm_server_destroy", "pm_polymul_noalloc",
@@ -476,3 +477,74 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# autotuner (pm_autotune, pm_batch_autotune)
+# ---------------------------------------------------------------------------
+
+PM_TUNE_MAX_CANDIDATES = 16
+
+
+class pm_tune_report(C.Structure):
+    _fields_ = [("count", C.c_uint32), ("best", C.c_uint32), ("candidates", pm_options * PM_TUNE_MAX_CANDIDATES),
+                ("ms", C.c_float * PM_TUNE_MAX_CANDIDATES)]
+
+
+class pm_batch_tune_report(C.Structure):
+    _fields_ = [("count", C.c_uint32), ("best", C.c_uint32), ("sample", C.c_uint32),
+                ("candidates", pm_batch_options * PM_TUNE_MAX_CANDIDATES), ("ms", C.c_float * PM_TUNE_MAX_CANDIDATES)]
+
+
+def _opts_dict(o: pm_options) -> dict:
+    return dict(strategy=STRATEGY_NAME.get(o.strategy, o.strategy), slots=o.slots, chunk=o.chunk,
+                ranges_per_sm=o.ranges_per_sm, accumulator={v: k for k, v in ACCUMULATOR.items()}.get(o.accumulator))
+
+
+def autotune(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61", stream=None):
+    """Time every candidate configuration on this product, keep the fastest
+    for its shape class (later pm_polymul calls with default options use it)
+    and return (best options dict, [(options dict, ms)])."""
+    import torch
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
+    L = lib()
+    L.pm_autotune.argtypes = [C.POINTER(pm_packing), C.c_int, C.POINTER(pm_terms_in), C.POINTER(pm_terms_in),
+                              C.POINTER(pm_terms_out), C.POINTER(pm_options), C.POINTER(pm_tune_report), C.c_void_p]
+    L.pm_autotune.restype = C.c_int
+    cap = out_bound(field_bits, f_exps, g_exps, stream)
+    words = 1 if kind == "m61" else 2
+    keys = torch.empty(max(cap, 1), dtype=torch.int64, device=f_exps.device)
+    coefs = torch.empty((max(cap, 1), 2) if words == 2 else (max(cap, 1),), dtype=torch.int64, device=f_exps.device)
+    h = pm_terms_out(keys.data_ptr(), coefs.data_ptr(), 0, cap)
+    best = pm_options()
+    rep = pm_tune_report()
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    rc = L.pm_autotune(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(best), C.byref(rep),
+                       _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_autotune")
+    table = [(_opts_dict(rep.candidates[k]), float(rep.ms[k])) for k in range(rep.count)]
+    return _opts_dict(best), table
+
+
+def batch_autotune(products, stream=None):
+    """Pick (range_target, ranges_per_item) for a batch by timing plans on a
+    sample of it; returns (best dict, [(candidate dict, ms)])."""
+    L = _batch_lib()
+    L.pm_batch_autotune.argtypes = [C.POINTER(pm_batch_item), C.c_uint32, C.POINTER(pm_batch_options),
+                                    C.POINTER(pm_batch_tune_report), C.c_void_p]
+    L.pm_batch_autotune.restype = C.c_int
+    n = len(products)
+    items = (pm_batch_item * n)()
+    for k, pr in enumerate(products):
+        items[k] = _batch_item(pr)
+    best = pm_batch_options()
+    rep = pm_batch_tune_report()
+    rc = L.pm_batch_autotune(items, n, C.byref(best), C.byref(rep), _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_batch_autotune")
+    table = [({"range_target": rep.candidates[k].range_target, "ranges_per_item": rep.candidates[k].ranges_per_item},
+              float(rep.ms[k])) for k in range(rep.count)]
+    return {"range_target": best.range_target, "ranges_per_item": best.ranges_per_item}, table

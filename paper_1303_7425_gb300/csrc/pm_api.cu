@@ -14,6 +14,8 @@
 
 namespace pm {
 
+bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box, pm_options &o);
+
 constexpr u32 DEFAULT_CHUNK = 4096;    // sort: term products per range
 constexpr u32 MAX_CHUNK = 4096;
 
@@ -177,6 +179,12 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (f->n == 0 || g->n == 0) return finish(0);
     Layout raw = L;
     const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
+    if (!opt || (!o.strategy && !o.slots && !o.chunk && !o.ranges_per_sm && !o.accumulator)) {
+        // default options: use the autotuner's choice for this shape class
+        const unsigned __int128 pr = (unsigned __int128)f->n * g->n;
+        const u64 bound = pr < raw_box ? (u64)pr : raw_box;
+        tuned_options(kind, L.nv, f->n, g->n, bound, o);
+    }
 
     // K-a (2): canonical operands, their maxima, extremes and sizes    [sync 2]
     Operand F, G;
