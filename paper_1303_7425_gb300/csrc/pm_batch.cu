@@ -343,8 +343,12 @@ struct RngSmem {
     u32 *hist;
 };
 
+// the histogram area doubles as the per-row offsets of a piece
+// (BT_MAX_TERMS + 1 u16), hence its 16 extra bytes
+constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256 + 4;
+static_assert(RNG_HIST_WORDS * 4 >= (BT_MAX_TERMS + 1) * 2, "row offsets overflow the histogram area");
 constexpr size_t RNG_SMEM = (size_t)BT_MAX_TERMS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
-                            (RNG_T / 32) * 256 * 4;
+                            RNG_HIST_WORDS * 4;
 
 __device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
 {
@@ -354,7 +358,7 @@ __device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
     m.kB = m.kA + RNG_CHUNK;
     m.cv = m.kB + RNG_CHUNK;
     m.hist = (u32 *)(m.cv + 2 * RNG_CHUNK);
-    m.cur = (uint16_t *)(m.hist + (RNG_T / 32) * 256);
+    m.cur = (uint16_t *)(m.hist + RNG_HIST_WORDS);
     m.iA = m.cur + BT_MAX_TERMS;
     m.iB = m.iA + RNG_CHUNK;
     return m;
@@ -368,24 +372,64 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
 {
     const u32 tid = threadIdx.x;
     const int kind = (int)d.kind;
+    // per-row offsets of the piece's products (rows of this thread are
+    // [r0, r1)); kept in the histogram area, which the sort reuses later
+    uint16_t *offs = (uint16_t *)m.hist;  // nrows + 1 entries (<= 8193 u16)
     u64 mine = 0;
     for (u32 r = r0; r < r1; r++) mine += jh[r - r0] - m.cur[r];
     u64 O;
     u64 base = block_exclusive_scan(mine, O, ws);
     for (u32 r = r0; r < r1; r++) {
-        const u64 a_key = A[r], a_c = Ac[r];
-        for (u32 j = m.cur[r]; j < jh[r - r0]; j++) {
-            const u32 q = (u32)base++;
-            if (q >= RNG_CHUNK) break;  // cannot happen: O <= RNG_CHUNK here
-            m.kA[q] = a_key + m.Bs[j];
-            m.iA[q] = (uint16_t)q;
-            if (kind == PM_COEF_M61) {
-                m.cv[q] = m61_reduce(m61_mul_lazy(a_c, Bc[j]));
-            } else {
-                u64 lo, hi;
-                mul_i64_wide((i64)a_c, (i64)Bc[j], lo, hi);
-                m.cv[q] = lo;
-                m.cv[RNG_CHUNK + q] = hi;
+        offs[r] = (uint16_t)base;
+        base += jh[r - r0] - m.cur[r];
+    }
+    if (threadIdx.x == 0) offs[cf] = (uint16_t)O;
+    __syncthreads();
+    // warp w takes a contiguous slice of the products, lanes interleaved so
+    // that neighbouring lanes read neighbouring columns; each lane follows
+    // its row with a forward walk over the offsets
+    {
+        const u32 lane = tid & 31, w = tid >> 5;
+        const u32 tot = (u32)O;
+        const u32 per_warp = ((tot + RNG_T / 32 - 1) / (RNG_T / 32) + 31u) & ~31u;
+        const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, tot);
+        u32 q = p0 + lane;
+        if (q < p1) {
+            u32 lo = 0, len = cf;  // last row with offs[row] <= q
+            while (len > 0) {
+                const u32 half = len >> 1;
+                if (offs[lo + half] <= q) {
+                    lo += half + 1;
+                    len -= half + 1;
+                } else {
+                    len = half;
+                }
+            }
+            u32 r = lo - 1;
+            u32 rend = offs[r + 1];
+            u64 a_key = A[r], a_c = Ac[r];
+            u32 jb = m.cur[r] - offs[r];
+            for (; q < p1; q += 32) {
+                if (q >= rend) {
+                    do {
+                        r++;
+                    } while (offs[r + 1] <= q);
+                    rend = offs[r + 1];
+                    a_key = A[r];
+                    a_c = Ac[r];
+                    jb = m.cur[r] - offs[r];
+                }
+                const u32 j = jb + q;
+                m.kA[q] = a_key + m.Bs[j];
+                m.iA[q] = (uint16_t)q;
+                if (kind == PM_COEF_M61) {
+                    m.cv[q] = m61_reduce(m61_mul_lazy(a_c, Bc[j]));
+                } else {
+                    u64 lo2, hi2;
+                    mul_i64_wide((i64)a_c, (i64)Bc[j], lo2, hi2);
+                    m.cv[q] = lo2;
+                    m.cv[RNG_CHUNK + q] = hi2;
+                }
             }
         }
     }
@@ -487,9 +531,14 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
         const BDesc &d = a.D[p];
         if (d.status || first >= d.nranges) continue;
         const u32 last = min(first + a.per_item, d.nranges);
-        const u32 cf = d.cf, cg = d.cg;
-        const u64 *A = a.ck + d.op_off, *Ac = a.cc + d.op_off;
-        const u64 *Bg = A + d.nf, *Bc = Ac + d.nf;
+        // rows run over the smaller operand (the product is commutative), so
+        // each range visits as few rows as possible
+        const bool swap = d.cf > d.cg;
+        const u32 cf = swap ? d.cg : d.cf, cg = swap ? d.cf : d.cg;
+        const u64 *Fk = a.ck + d.op_off, *Fc = a.cc + d.op_off;
+        const u64 *Gk = Fk + d.nf, *Gc = Fc + d.nf;
+        const u64 *A = swap ? Gk : Fk, *Ac = swap ? Gc : Fc;
+        const u64 *Bg = swap ? Fk : Gk, *Bc = swap ? Fc : Gc;
         for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
         __syncthreads();
         // rows of this thread: [r0, r1); cursors at the first range's start
