@@ -435,7 +435,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     }
     __syncthreads();
     const u32 n = (u32)(O < RNG_CHUNK ? O : RNG_CHUNK);
-    block_sort_pairs<RNG_T, RNG_IPT>(m.kA, m.iA, m.kB, m.iB, n, varying_bits(plo, phi - 1), m.hist, ws);
+    block_sort_interval<RNG_T, RNG_IPT>(m.kA, m.iA, m.kB, m.iB, n, plo, phi - 1 - plo, m.hist, ws);
     u64 run = 0;
     for (u32 t0 = 0; t0 < n; t0 += RNG_T) {
         const u32 i = t0 + tid;
@@ -541,8 +541,10 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
         const u64 *Bg = swap ? Fk : Gk, *Bc = swap ? Fc : Gc;
         for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
         __syncthreads();
-        // rows of this thread: [r0, r1); cursors at the first range's start
-        const u32 r0 = min(tid * ROWS_PER_T, cf), r1 = min(r0 + ROWS_PER_T, cf);
+        // rows of this thread: [r0, r1), ceil(cf / RNG_T) <= ROWS_PER_T of
+        // them, so every thread has work; cursors at the first range's start
+        const u32 rpt = (cf + RNG_T - 1) / RNG_T;
+        const u32 r0 = min(tid * rpt, cf), r1 = min(r0 + rpt, cf);
         u32 jh[ROWS_PER_T];
         {
             const u64 lo = a.rlo[d.rg_off + first];

@@ -1,4 +1,5 @@
-// Block-wide stable LSD radix sort of (key, index) pairs in shared memory.
+// Block-wide sorts of (key, index) pairs in shared memory: a stable LSD
+// radix sort, and a bucket sort for keys drawn from a known interval.
 #pragma once
 
 #include "pm_common.cuh"
@@ -84,6 +85,111 @@ __device__ __forceinline__ int varying_bits(u64 lo, u64 hi_inclusive)
         x >>= 1;
     }
     return b;
+}
+
+constexpr u32 BUCKETS = 4096;     // bucket-sort buckets (hist words it needs)
+constexpr u32 BUCKET_INSERT_MAX = 32;  // larger buckets: fall back to the radix sort
+
+// Sorts n <= THREADS * IPT pairs whose keys lie in [lo, lo + span].  The
+// pairs are distributed over 4096 buckets on the top 12 significant bits of
+// key - lo, and each bucket is then ordered by an insertion sort (one thread
+// per bucket); when span < 4096 a bucket holds one key value and needs no
+// second step.  One counting pass and one scatter replace the 8-bit passes
+// of the radix sort, which for sparse products (keys spread over 50 and
+// more bits) are 7 or 8.  Equal keys come out adjacent but in no particular
+// order, so callers must only combine them with an exact (order-free) sum.
+// When a bucket holds more than BUCKET_INSERT_MAX pairs (keys clustered
+// inside the interval) the radix sort runs instead.  hist: at least
+// max(4096, THREADS / 32 * 256) words; ws: 32 words.  All threads must call.
+template <int THREADS, int IPT, class I>
+__device__ void block_sort_interval(u64 *&kA, I *&iA, u64 *&kB, I *&iB, u32 n, u64 lo, u64 span, u32 *hist,
+                                    u64 *ws)
+{
+    static_assert(BUCKETS % THREADS == 0, "buckets per thread");
+    constexpr u32 PER = BUCKETS / THREADS;
+    __shared__ u32 s_bmax;
+    const u32 tid = threadIdx.x, lane = tid & 31;
+    int nb = 0;
+    for (u64 x = span; x; x >>= 1) nb++;
+    const int shift = nb > 12 ? nb - 12 : 0;
+    for (u32 x = tid; x < BUCKETS; x += THREADS) hist[x] = 0;
+    if (tid == 0) s_bmax = 0;
+    __syncthreads();
+    // count, one shared-memory atomic per distinct bucket of a warp
+    const u32 nround = (n + 31u) & ~31u;
+    for (u32 i = tid & ~31u; i < nround; i += THREADS) {
+        const u32 q = i + lane;
+        const bool valid = q < n;
+        const u32 b = valid ? (u32)min((kA[q] - lo) >> shift, (u64)BUCKETS - 1) : BUCKETS;
+        const u32 peers = __match_any_sync(0xffffffffu, b);
+        if (valid && lane == (u32)(__ffs(peers) - 1)) atomicAdd(&hist[b], (u32)__popc(peers));
+    }
+    __syncthreads();
+    // exclusive offsets (thread t owns buckets [t PER, t PER + PER)) and the
+    // largest bucket
+    u32 c[PER];
+    u32 sum = 0, mx = 0;
+#pragma unroll
+    for (u32 q = 0; q < PER; q++) {
+        c[q] = hist[tid * PER + q];
+        sum += c[q];
+        mx = c[q] > mx ? c[q] : mx;
+    }
+    if (mx > BUCKET_INSERT_MAX) atomicMax(&s_bmax, mx);
+    u64 tot;
+    u32 run = (u32)block_exclusive_scan(sum, tot, ws);
+#pragma unroll
+    for (u32 q = 0; q < PER; q++) {
+        hist[tid * PER + q] = run;
+        run += c[q];
+    }
+    __syncthreads();
+    if (shift > 0 && s_bmax > BUCKET_INSERT_MAX) {
+        block_sort_pairs<THREADS, IPT>(kA, iA, kB, iB, n, varying_bits(lo, lo + span), hist, ws);
+        return;
+    }
+    // scatter; afterwards hist[b] is the end of bucket b
+    for (u32 i = tid & ~31u; i < nround; i += THREADS) {
+        const u32 q = i + lane;
+        const bool valid = q < n;
+        const u64 key = valid ? kA[q] : 0;
+        const u32 b = valid ? (u32)min((key - lo) >> shift, (u64)BUCKETS - 1) : BUCKETS;
+        const u32 peers = __match_any_sync(0xffffffffu, b);
+        const u32 leader = (u32)(__ffs(peers) - 1);
+        u32 base = 0;
+        if (valid && lane == leader) base = atomicAdd(&hist[b], (u32)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (valid) {
+            const u32 pos = base + (u32)__popc(peers & ((1u << lane) - 1u));
+            kB[pos] = key;
+            iB[pos] = iA[q];
+        }
+    }
+    __syncthreads();
+    if (shift > 0) {
+        for (u32 b = tid; b < BUCKETS; b += THREADS) {
+            const u32 beg = b ? hist[b - 1] : 0u, end = hist[b];
+            for (u32 x = beg + 1; x < end; x++) {
+                const u64 k = kB[x];
+                const I v = iB[x];
+                u32 y = x;
+                while (y > beg && kB[y - 1] > k) {
+                    kB[y] = kB[y - 1];
+                    iB[y] = iB[y - 1];
+                    y--;
+                }
+                kB[y] = k;
+                iB[y] = v;
+            }
+        }
+        __syncthreads();
+    }
+    u64 *tk = kA;
+    kA = kB;
+    kB = tk;
+    I *ti = iA;
+    iA = iB;
+    iB = ti;
 }
 
 }  // namespace pm

@@ -7,11 +7,12 @@
 // (2) forms the range's term products, staging per-row data in shared memory
 //     and reading the other operand's coefficients with coalesced loads,
 // (3) accumulates them in shared memory -- the "MergeSort" of Alg. 1 -- with
-//     an LSD radix sort of the range's (key, product) pairs on the bits
-//     that vary inside [lo, hi), then a segmented reduction (the
-//     direct-addressed strategy lives in pm_direct.cu),
+//     a bucket sort of the range's (key, product) pairs on the top bits of
+//     key - lo (radix sort where keys cluster), then a segmented reduction
+//     (the direct-addressed strategy lives in pm_direct.cu),
 // (4) writes its non-zero terms in ascending order to the range's slice of
 //     the output scratch (concatenation happens in K-e).
+#include "pm_blocksort.cuh"
 #include "pm_range.cuh"
 
 namespace pm {
@@ -135,70 +136,6 @@ __device__ __forceinline__ SortSmem carve_sort(unsigned char *p, u32 chunk, int 
     return m;
 }
 
-// stable LSD sort of n <= chunk (key, index) pairs on bits [0, nbits)
-__device__ void block_radix_sort(SortSmem &m, u32 n, int nbits, u64 *ws)
-{
-    const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const u32 ipt = (n + RK_THREADS - 1) / RK_THREADS;  // <= SORT_IPT_MAX
-    u32 *hist = m.hist;
-    for (int shift = 0; shift < nbits; shift += 8) {
-        for (u32 x = tid; x < RK_WARPS * 256; x += RK_THREADS) hist[x] = 0;
-        __syncthreads();
-        u32 rank[SORT_IPT_MAX], dig[SORT_IPT_MAX];
-#pragma unroll
-        for (int s = 0; s < SORT_IPT_MAX; s++) {
-            if ((u32)s < ipt) {
-                const u32 i = w * 32 * ipt + s * 32 + lane;
-                const bool valid = i < n;
-                const u32 d = valid ? (u32)((m.kA[i] >> shift) & 255u) : 256u;
-                const u32 peers = __match_any_sync(0xffffffffu, d);
-                const u32 lt = __popc(peers & ((1u << lane) - 1u));
-                const u32 base = valid ? hist[w * 256 + d] : 0u;
-                __syncwarp();
-                if (valid && lt == 0) hist[w * 256 + d] = base + __popc(peers);
-                __syncwarp();
-                rank[s] = base + lt;
-                dig[s] = d;
-            }
-        }
-        __syncthreads();
-        // digit-major, warp-minor exclusive offsets
-        u64 dsum = 0;
-        if (tid < 256) {
-            u32 run = 0;
-            for (int ww = 0; ww < RK_WARPS; ww++) {
-                u32 c = hist[ww * 256 + tid];
-                hist[ww * 256 + tid] = run;
-                run += c;
-            }
-            dsum = run;
-        }
-        u64 tot;
-        u64 dbase = block_exclusive_scan(dsum, tot, ws);
-        if (tid < 256)
-            for (int ww = 0; ww < RK_WARPS; ww++) hist[ww * 256 + tid] += (u32)dbase;
-        __syncthreads();
-#pragma unroll
-        for (int s = 0; s < SORT_IPT_MAX; s++) {
-            if ((u32)s < ipt) {
-                const u32 i = w * 32 * ipt + s * 32 + lane;
-                if (i < n) {
-                    const u32 pos = hist[w * 256 + dig[s]] + rank[s];
-                    m.kB[pos] = m.kA[i];
-                    m.iB[pos] = m.iA[i];
-                }
-            }
-        }
-        __syncthreads();
-        u64 *tk = m.kA;
-        m.kA = m.kB;
-        m.kB = tk;
-        uint16_t *ti = m.iA;
-        m.iA = m.iB;
-        m.iB = ti;
-    }
-}
-
 template <int KIND>
 __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chunk)
 {
@@ -300,10 +237,9 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
         if (filled != O && tid == 0) atomicOr(a.status, ST_INTERNAL);
         const u32 n = filled < chunk ? filled : chunk;
 
-        // (3) sort on the bits that vary inside [lo, hi), then reduce runs
-        int nbits = 0;
-        for (u64 x = hi - 1 - lo; x; x >>= 1) nbits++;
-        block_radix_sort(m, n, nbits, ws);
+        // (3) sort the keys (relative to lo, so inside [0, hi - 1 - lo]),
+        // then reduce runs
+        block_sort_interval<RK_THREADS, SORT_IPT_MAX>(m.kA, m.iA, m.kB, m.iB, n, 0, hi - 1 - lo, m.hist, ws);
 
         u64 run = 0;
         for (u32 c0 = 0; c0 < n; c0 += RK_THREADS) {
