@@ -36,6 +36,8 @@ constexpr u32 PLAN_SAMPLES = 8192;
 constexpr int RNG_T = 512;                        // B3 threads
 constexpr u32 RNG_CHUNK = 3072;                   // products sorted per piece
 constexpr int RNG_IPT = RNG_CHUNK / RNG_T;
+constexpr u32 RNG_W = RNG_T / 32;
+constexpr u32 RNG_LANE_MAX = (RNG_CHUNK / RNG_W + 31) / 32;  // products (or pairs) per lane of a piece
 constexpr u32 ROWS_PER_T = BT_MAX_TERMS / RNG_T;  // 16
 constexpr int FIN_T = 512;
 
@@ -366,9 +368,11 @@ __device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
 
 // One piece [plo, phi) whose column edges are cur (start) and jh (end, per
 // thread's rows): generate its O <= RNG_CHUNK products, sort, reduce, and
-// write the non-zero terms at out + written.  Returns the terms written.
+// write the non-zero terms at claim_r + written, claim_r being the range's
+// output base as thread 0 holds it.  Returns the terms written.
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
-                         u32 cf, u32 r0, u32 r1, const u32 *jh, u64 plo, u64 phi, u64 out, u64 *ws)
+                         u32 cf, u32 r0, u32 r1, const u32 *jh, u64 plo, u64 phi, u64 claim_r, u64 written,
+                         u64 *s_out, u64 *ws)
 {
     const u32 tid = threadIdx.x;
     const int kind = (int)d.kind;
@@ -386,49 +390,47 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     if (threadIdx.x == 0) offs[cf] = (uint16_t)O;
     __syncthreads();
     // warp w takes a contiguous slice of the products, lanes interleaved so
-    // that neighbouring lanes read neighbouring columns; each lane follows
-    // its row with a forward walk over the offsets
+    // that neighbouring lanes read neighbouring columns.  A lane first finds
+    // the rows of all its products, then issues their loads together, so
+    // the global-load latency is paid once per piece.
+    const u32 lane = tid & 31, w = tid >> 5;
     {
-        const u32 lane = tid & 31, w = tid >> 5;
         const u32 tot = (u32)O;
-        const u32 per_warp = ((tot + RNG_T / 32 - 1) / (RNG_T / 32) + 31u) & ~31u;
+        const u32 per_warp = ((tot + RNG_W - 1) / RNG_W + 31u) & ~31u;
         const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, tot);
-        u32 q = p0 + lane;
-        if (q < p1) {
-            u32 lo = 0, len = cf;  // last row with offs[row] <= q
-            while (len > 0) {
-                const u32 half = len >> 1;
-                if (offs[lo + half] <= q) {
-                    lo += half + 1;
-                    len -= half + 1;
-                } else {
-                    len = half;
-                }
+        u32 rr[RNG_LANE_MAX], jj[RNG_LANE_MAX];
+        const u32 q0 = p0 + lane;
+        if (q0 < p1) {
+            // row of each product: last r in [0, cf) with offs[r] <= q, by
+            // branch-free binary searches run side by side (a product's row
+            // is typically a dozen rows past its neighbour's, 32 products
+            // earlier, so a forward walk would chain that many loads)
+#pragma unroll
+            for (u32 t = 0; t < RNG_LANE_MAX; t++) rr[t] = 0;
+            for (u32 nn = cf; nn > 1;) {
+                const u32 half = nn >> 1;
+#pragma unroll
+                for (u32 t = 0; t < RNG_LANE_MAX; t++)
+                    if (offs[rr[t] + half] <= q0 + 32 * t) rr[t] += half;
+                nn -= half;
             }
-            u32 r = lo - 1;
-            u32 rend = offs[r + 1];
-            u64 a_key = A[r], a_c = Ac[r];
-            u32 jb = m.cur[r] - offs[r];
-            for (; q < p1; q += 32) {
-                if (q >= rend) {
-                    do {
-                        r++;
-                    } while (offs[r + 1] <= q);
-                    rend = offs[r + 1];
-                    a_key = A[r];
-                    a_c = Ac[r];
-                    jb = m.cur[r] - offs[r];
-                }
-                const u32 j = jb + q;
-                m.kA[q] = a_key + m.Bs[j];
-                m.iA[q] = (uint16_t)q;
-                if (kind == PM_COEF_M61) {
-                    m.cv[q] = m61_reduce(m61_mul_lazy(a_c, Bc[j]));
-                } else {
-                    u64 lo2, hi2;
-                    mul_i64_wide((i64)a_c, (i64)Bc[j], lo2, hi2);
-                    m.cv[q] = lo2;
-                    m.cv[RNG_CHUNK + q] = hi2;
+#pragma unroll
+            for (u32 t = 0; t < RNG_LANE_MAX; t++) jj[t] = m.cur[rr[t]] - offs[rr[t]] + q0 + 32 * t;
+#pragma unroll
+            for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+                const u32 q = q0 + 32 * t;
+                if (q < p1) {
+                    const u32 r2 = rr[t], j = jj[t];
+                    m.kA[q] = A[r2] + m.Bs[j];
+                    m.iA[q] = (uint16_t)q;
+                    if (kind == PM_COEF_M61) {
+                        m.cv[q] = m61_reduce(m61_mul_lazy(Ac[r2], Bc[j]));
+                    } else {
+                        u64 lo2, hi2;
+                        mul_i64_wide((i64)Ac[r2], (i64)Bc[j], lo2, hi2);
+                        m.cv[q] = lo2;
+                        m.cv[RNG_CHUNK + q] = hi2;
+                    }
                 }
             }
         }
@@ -436,31 +438,54 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     __syncthreads();
     const u32 n = (u32)(O < RNG_CHUNK ? O : RNG_CHUNK);
     block_sort_interval<RNG_T, RNG_IPT>(m.kA, m.iA, m.kB, m.iB, n, plo, phi - 1 - plo, m.hist, ws);
-    u64 run = 0;
-    for (u32 t0 = 0; t0 < n; t0 += RNG_T) {
-        const u32 i = t0 + tid;
-        u64 v0 = 0, v1 = 0;
+    // segmented reduction: warp w owns the run heads in a contiguous
+    // segment of the sorted pairs (a run may continue past it); positions
+    // come from ballots and one block scan over the warps' counts
+    const u32 seg = ((n + RNG_W - 1) / RNG_W + 31u) & ~31u;
+    const u32 s0 = w * seg, s1 = min(s0 + seg, n);
+    u64 v0[RNG_LANE_MAX], v1[RNG_LANE_MAX];
+    u32 nzmask[RNG_LANE_MAX];
+    u32 wcount = 0;
+#pragma unroll
+    for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+        const u32 i = s0 + 32 * t + lane;
+        v0[t] = 0;
+        v1[t] = 0;
         bool nz = false;
-        if (i < n && (i == 0 || m.kA[i] != m.kA[i - 1])) {
-            for (u32 j = i; j < n && m.kA[j] == m.kA[i]; j++) {
-                const u32 s = m.iA[j];
-                if (kind == PM_COEF_M61) v0 = m61_add(v0, m.cv[s]);
-                else add128(v0, v1, m.cv[s], m.cv[RNG_CHUNK + s]);
+        if (i < s1 && (i == 0 || m.kA[i] != m.kA[i - 1])) {
+            const u64 key = m.kA[i];
+            for (u32 j = i; j < n && m.kA[j] == key; j++) {
+                const u32 src = m.iA[j];
+                if (kind == PM_COEF_M61) v0[t] = m61_add(v0[t], m.cv[src]);
+                else add128(v0[t], v1[t], m.cv[src], m.cv[RNG_CHUNK + src]);
             }
-            nz = (v0 | v1) != 0;
+            nz = (v0[t] | v1[t]) != 0;
         }
-        u64 cnt;
-        const u64 pos = block_exclusive_scan(nz ? 1 : 0, cnt, ws);
-        if (nz) {
-            const u64 dst = out + run + pos;
+        nzmask[t] = __ballot_sync(0xffffffffu, nz);
+        wcount += (u32)__popc(nzmask[t]);
+    }
+    // thread 0 publishes the output base here, so the claim's atomic
+    // (issued before the piece was generated) is waited for only now; the
+    // scan's barriers make it visible
+    if (tid == 0) *s_out = claim_r + written;
+    u64 total;
+    u64 wbase = block_exclusive_scan(lane == 0 ? wcount : 0u, total, ws);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+    const u64 out = *s_out;
+    u32 before = 0;
+#pragma unroll
+    for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+        const u32 i = s0 + 32 * t + lane;
+        if ((nzmask[t] >> lane) & 1u) {
+            const u64 dst = out + wbase + before + (u32)__popc(nzmask[t] & ((1u << lane) - 1u));
             a.skey[dst] = m.kA[i];
-            a.scoef[a.cw * dst] = v0;
-            if (a.cw == 2) a.scoef[2 * dst + 1] = v1;
+            a.scoef[a.cw * dst] = v0[t];
+            if (a.cw == 2) a.scoef[2 * dst + 1] = v1[t];
         }
-        run += cnt;
+        before += (u32)__popc(nzmask[t]);
     }
     __syncthreads();
-    return run;
+    return total;
 }
 
 // sum of all products of a single-monomial piece with more than RNG_CHUNK
@@ -581,13 +606,13 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
             }
             u64 O;
             block_exclusive_scan(mine, O, ws);
-            // claim the range's output space (at most O terms)
-            if (tid == 0) claim = atomicAdd(a.bump, O);
-            __syncthreads();
-            const u64 out = claim;
+            // claim the range's output space (at most O terms); only thread
+            // 0 holds the base, and waits for it when a piece publishes it
+            u64 claim_r = 0;
+            if (tid == 0) claim_r = atomicAdd(a.bump, O);
             u64 written = 0;
             if (O <= RNG_CHUNK) {
-                if (O) written = rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, rlo_k, rhi_k, out, ws);
+                if (O) written = rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, rlo_k, rhi_k, claim_r, 0, &claim, ws);
                 for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
                 __syncthreads();
             } else {
@@ -607,11 +632,13 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
                         u64 PO;
                         block_exclusive_scan(cnt_mine, PO, ws);
                         if (PO <= RNG_CHUNK) {
-                            if (PO) written += rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, plo, phi, out + written, ws);
+                            if (PO)
+                                written += rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, plo, phi, claim_r, written,
+                                                     &claim, ws);
                             break;
                         }
                         if (phi - plo == 1) {
-                            written += rng_single(a, d, m, A, Ac, Bc, r0, r1, jh, plo, out + written, ws);
+                            written += rng_single(a, d, m, A, Ac, Bc, r0, r1, jh, plo, claim_r + written, ws);
                             break;
                         }
                         phi = plo + (phi - plo) / 2;
@@ -622,7 +649,7 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
                 }
             }
             if (tid == 0) {
-                a.rbase[d.rg_off + k] = out;
+                a.rbase[d.rg_off + k] = claim_r;
                 a.rcount[d.rg_off + k] = written;
             }
         }

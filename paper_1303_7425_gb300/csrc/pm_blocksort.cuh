@@ -88,19 +88,21 @@ __device__ __forceinline__ int varying_bits(u64 lo, u64 hi_inclusive)
 }
 
 constexpr u32 BUCKETS = 4096;     // bucket-sort buckets (hist words it needs)
-constexpr u32 BUCKET_INSERT_MAX = 32;  // larger buckets: fall back to the radix sort
+constexpr u32 BUCKET_RANK_MAX = 32;  // larger buckets: fall back to the radix sort
 
 // Sorts n <= THREADS * IPT pairs whose keys lie in [lo, lo + span].  The
 // pairs are distributed over 4096 buckets on the top 12 significant bits of
-// key - lo, and each bucket is then ordered by an insertion sort (one thread
-// per bucket); when span < 4096 a bucket holds one key value and needs no
-// second step.  One counting pass and one scatter replace the 8-bit passes
-// of the radix sort, which for sparse products (keys spread over 50 and
-// more bits) are 7 or 8.  Equal keys come out adjacent but in no particular
-// order, so callers must only combine them with an exact (order-free) sum.
-// When a bucket holds more than BUCKET_INSERT_MAX pairs (keys clustered
-// inside the interval) the radix sort runs instead.  hist: at least
-// max(4096, THREADS / 32 * 256) words; ws: 32 words.  All threads must call.
+// key - lo; each pair then finds its place inside its bucket by counting
+// the bucket's smaller keys (ties by position), so every pair moves twice
+// and no thread works on more than one bucket's worth of compares per pair.
+// When span < 4096 a bucket holds one key value and the scatter alone
+// sorts.  For sparse products (keys spread over 50 and more bits) this
+// replaces the 7 or 8 passes of an 8-bit radix sort.  Equal keys come out
+// adjacent but in no particular order, so callers must only combine them
+// with an exact (order-free) sum.  When a bucket holds more than
+// BUCKET_RANK_MAX pairs (keys clustered inside the interval) the radix sort
+// runs instead.  hist: at least max(4096, THREADS / 32 * 256) words; ws: 32
+// words.  All threads must call.
 template <int THREADS, int IPT, class I>
 __device__ void block_sort_interval(u64 *&kA, I *&iA, u64 *&kB, I *&iB, u32 n, u64 lo, u64 span, u32 *hist,
                                     u64 *ws)
@@ -115,14 +117,20 @@ __device__ void block_sort_interval(u64 *&kA, I *&iA, u64 *&kB, I *&iB, u32 n, u
     for (u32 x = tid; x < BUCKETS; x += THREADS) hist[x] = 0;
     if (tid == 0) s_bmax = 0;
     __syncthreads();
-    // count, one shared-memory atomic per distinct bucket of a warp
     const u32 nround = (n + 31u) & ~31u;
-    for (u32 i = tid & ~31u; i < nround; i += THREADS) {
-        const u32 q = i + lane;
-        const bool valid = q < n;
-        const u32 b = valid ? (u32)min((kA[q] - lo) >> shift, (u64)BUCKETS - 1) : BUCKETS;
-        const u32 peers = __match_any_sync(0xffffffffu, b);
-        if (valid && lane == (u32)(__ffs(peers) - 1)) atomicAdd(&hist[b], (u32)__popc(peers));
+    if (shift > 0) {
+        // spread keys: few collisions, one atomic per pair
+        for (u32 q = tid; q < n; q += THREADS) atomicAdd(&hist[(u32)min((kA[q] - lo) >> shift, (u64)BUCKETS - 1)], 1u);
+    } else {
+        // one key value per bucket, often repeated: one atomic per distinct
+        // bucket of a warp
+        for (u32 i = tid & ~31u; i < nround; i += THREADS) {
+            const u32 q = i + lane;
+            const bool valid = q < n;
+            const u32 b = valid ? (u32)min(kA[q] - lo, (u64)BUCKETS - 1) : BUCKETS;
+            const u32 peers = __match_any_sync(0xffffffffu, b);
+            if (valid && lane == (u32)(__ffs(peers) - 1)) atomicAdd(&hist[b], (u32)__popc(peers));
+        }
     }
     __syncthreads();
     // exclusive offsets (thread t owns buckets [t PER, t PER + PER)) and the
@@ -135,7 +143,7 @@ __device__ void block_sort_interval(u64 *&kA, I *&iA, u64 *&kB, I *&iB, u32 n, u
         sum += c[q];
         mx = c[q] > mx ? c[q] : mx;
     }
-    if (mx > BUCKET_INSERT_MAX) atomicMax(&s_bmax, mx);
+    if (mx > BUCKET_RANK_MAX) atomicMax(&s_bmax, mx);
     u64 tot;
     u32 run = (u32)block_exclusive_scan(sum, tot, ws);
 #pragma unroll
@@ -144,52 +152,61 @@ __device__ void block_sort_interval(u64 *&kA, I *&iA, u64 *&kB, I *&iB, u32 n, u
         run += c[q];
     }
     __syncthreads();
-    if (shift > 0 && s_bmax > BUCKET_INSERT_MAX) {
+    if (shift > 0 && s_bmax > BUCKET_RANK_MAX) {
         block_sort_pairs<THREADS, IPT>(kA, iA, kB, iB, n, varying_bits(lo, lo + span), hist, ws);
         return;
     }
     // scatter; afterwards hist[b] is the end of bucket b
-    for (u32 i = tid & ~31u; i < nround; i += THREADS) {
-        const u32 q = i + lane;
-        const bool valid = q < n;
-        const u64 key = valid ? kA[q] : 0;
-        const u32 b = valid ? (u32)min((key - lo) >> shift, (u64)BUCKETS - 1) : BUCKETS;
-        const u32 peers = __match_any_sync(0xffffffffu, b);
-        const u32 leader = (u32)(__ffs(peers) - 1);
-        u32 base = 0;
-        if (valid && lane == leader) base = atomicAdd(&hist[b], (u32)__popc(peers));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (valid) {
-            const u32 pos = base + (u32)__popc(peers & ((1u << lane) - 1u));
+    if (shift > 0) {
+        for (u32 q = tid; q < n; q += THREADS) {
+            const u64 key = kA[q];
+            const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
+            const u32 pos = atomicAdd(&hist[b], 1u);
             kB[pos] = key;
             iB[pos] = iA[q];
         }
-    }
-    __syncthreads();
-    if (shift > 0) {
-        for (u32 b = tid; b < BUCKETS; b += THREADS) {
-            const u32 beg = b ? hist[b - 1] : 0u, end = hist[b];
-            for (u32 x = beg + 1; x < end; x++) {
-                const u64 k = kB[x];
-                const I v = iB[x];
-                u32 y = x;
-                while (y > beg && kB[y - 1] > k) {
-                    kB[y] = kB[y - 1];
-                    iB[y] = iB[y - 1];
-                    y--;
-                }
-                kB[y] = k;
-                iB[y] = v;
+    } else {
+        for (u32 i = tid & ~31u; i < nround; i += THREADS) {
+            const u32 q = i + lane;
+            const bool valid = q < n;
+            const u64 key = valid ? kA[q] : 0;
+            const u32 b = valid ? (u32)min(key - lo, (u64)BUCKETS - 1) : BUCKETS;
+            const u32 peers = __match_any_sync(0xffffffffu, b);
+            const u32 leader = (u32)(__ffs(peers) - 1);
+            u32 base = 0;
+            if (valid && lane == leader) base = atomicAdd(&hist[b], (u32)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (valid) {
+                const u32 pos = base + (u32)__popc(peers & ((1u << lane) - 1u));
+                kB[pos] = key;
+                iB[pos] = iA[q];
             }
         }
-        __syncthreads();
     }
-    u64 *tk = kA;
-    kA = kB;
-    kB = tk;
-    I *ti = iA;
-    iA = iB;
-    iB = ti;
+    __syncthreads();
+    if (shift == 0) {
+        u64 *tk = kA;
+        kA = kB;
+        kB = tk;
+        I *ti = iA;
+        iA = iB;
+        iB = ti;
+        return;
+    }
+    // rank inside the bucket, written back to the A buffers
+    for (u32 x = tid; x < n; x += THREADS) {
+        const u64 key = kB[x];
+        const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
+        const u32 beg = b ? hist[b - 1] : 0u, end = hist[b];
+        u32 rank = 0;
+        for (u32 y = beg; y < end; y++) {
+            const u64 o = kB[y];
+            rank += (o < key || (o == key && y < x)) ? 1u : 0u;
+        }
+        kA[beg + rank] = key;
+        iA[beg + rank] = iB[x];
+    }
+    __syncthreads();
 }
 
 }  // namespace pm
