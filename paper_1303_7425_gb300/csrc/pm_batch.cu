@@ -345,10 +345,8 @@ struct RngSmem {
     u32 *hist;
 };
 
-// the histogram area doubles as the per-row offsets of a piece
-// (BT_MAX_TERMS + 1 u16), hence its 16 extra bytes
-constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256 + 4;
-static_assert(RNG_HIST_WORDS * 4 >= (BT_MAX_TERMS + 1) * 2, "row offsets overflow the histogram area");
+// sort histogram; also holds a piece's compacted row tables
+constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256;
 constexpr size_t RNG_SMEM = (size_t)BT_MAX_TERMS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
                             RNG_HIST_WORDS * 4;
 
@@ -366,56 +364,88 @@ __device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
     return m;
 }
 
+// A piece's rows that have products, compacted: the c-th such row is
+// crow[c] and its products start at coff[c] (coff[nnz] = O).  Both live in
+// the histogram area, which the sort reuses once the products are
+// generated.  The scan of the packed per-thread counts (products in the low
+// word, rows with products in the high word) gives this thread's starts.
+// rng_piece's first barrier publishes the tables.
+constexpr u32 RNG_CROW = RNG_CHUNK + 8;  // u16 offset of crow in the area
+static_assert((RNG_CROW + RNG_CHUNK) * 2 <= RNG_HIST_WORDS * 4, "row tables overflow the histogram area");
+
+__device__ __forceinline__ u64 row_counts(u32 cnt) { return (u64)cnt | ((u64)(cnt != 0) << 32); }
+
+__device__ __forceinline__ void piece_offsets(RngSmem &m, u32 r0, u32 r1, const u32 *jh, u64 base, u64 total)
+{
+    uint16_t *coff = (uint16_t *)m.hist, *crow = coff + RNG_CROW;
+    u32 pb = (u32)base, cb = (u32)(base >> 32);
+    for (u32 r = r0; r < r1; r++) {
+        const u32 cnt = jh[r - r0] - m.cur[r];
+        if (cnt) {
+            coff[cb] = (uint16_t)pb;
+            crow[cb] = (uint16_t)r;
+            cb++;
+            pb += cnt;
+        }
+    }
+    if (threadIdx.x == 0) coff[total >> 32] = (uint16_t)total;
+}
+
 // One piece [plo, phi) whose column edges are cur (start) and jh (end, per
-// thread's rows): generate its O <= RNG_CHUNK products, sort, reduce, and
-// write the non-zero terms at claim_r + written, claim_r being the range's
-// output base as thread 0 holds it.  Returns the terms written.
+// thread's rows), with offsets from piece_offsets: generate its
+// O <= RNG_CHUNK products, sort, reduce, and write the non-zero terms at
+// claim_r + written, claim_r being the range's output base as thread 0
+// holds it.  Returns the terms written.  Ends without a barrier: the
+// caller's next scan separates this piece's reads of the shared buffers
+// from the next piece's writes.
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
-                         u32 cf, u32 r0, u32 r1, const u32 *jh, u64 plo, u64 phi, u64 claim_r, u64 written,
-                         u64 *s_out, u64 *ws)
+                         u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws)
 {
     const u32 tid = threadIdx.x;
     const int kind = (int)d.kind;
-    // per-row offsets of the piece's products (rows of this thread are
-    // [r0, r1)); kept in the histogram area, which the sort reuses later
-    uint16_t *offs = (uint16_t *)m.hist;  // nrows + 1 entries (<= 8193 u16)
-    u64 mine = 0;
-    for (u32 r = r0; r < r1; r++) mine += jh[r - r0] - m.cur[r];
-    u64 O;
-    u64 base = block_exclusive_scan(mine, O, ws);
-    for (u32 r = r0; r < r1; r++) {
-        offs[r] = (uint16_t)base;
-        base += jh[r - r0] - m.cur[r];
-    }
-    if (threadIdx.x == 0) offs[cf] = (uint16_t)O;
+    const u32 O = (u32)total, nnz = (u32)(total >> 32);
+    const uint16_t *coff = (const uint16_t *)m.hist, *crow = coff + RNG_CROW;
     __syncthreads();
     // warp w takes a contiguous slice of the products, lanes interleaved so
-    // that neighbouring lanes read neighbouring columns.  A lane first finds
-    // the rows of all its products, then issues their loads together, so
-    // the global-load latency is paid once per piece.
+    // that neighbouring lanes read neighbouring columns.  The warp first
+    // finds the rows of all its products, then issues their loads together,
+    // so the global-load latency is paid once per piece.
     const u32 lane = tid & 31, w = tid >> 5;
     {
-        const u32 tot = (u32)O;
-        const u32 per_warp = ((tot + RNG_W - 1) / RNG_W + 31u) & ~31u;
-        const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, tot);
+        const u32 per_warp = ((O + RNG_W - 1) / RNG_W + 31u) & ~31u;
+        const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, O);
         u32 rr[RNG_LANE_MAX], jj[RNG_LANE_MAX];
         const u32 q0 = p0 + lane;
-        if (q0 < p1) {
-            // row of each product: last r in [0, cf) with offs[r] <= q, by
-            // branch-free binary searches run side by side (a product's row
-            // is typically a dozen rows past its neighbour's, 32 products
-            // earlier, so a forward walk would chain that many loads)
-#pragma unroll
-            for (u32 t = 0; t < RNG_LANE_MAX; t++) rr[t] = 0;
-            for (u32 nn = cf; nn > 1;) {
-                const u32 half = nn >> 1;
-#pragma unroll
-                for (u32 t = 0; t < RNG_LANE_MAX; t++)
-                    if (offs[rr[t] + half] <= q0 + 32 * t) rr[t] += half;
-                nn -= half;
+        if (p0 < p1) {
+            // compacted row holding product p0 (last c with coff[c] <= p0),
+            // by a 32-way search: each round every lane probes one point
+            u32 ca = 0, n = nnz;
+            while (n > 1) {
+                const u32 step = (n + 31) >> 5;
+                const bool le = lane * step < n && coff[ca + lane * step] <= p0;
+                const u32 k = 31 - __clz(__ballot_sync(0xffffffffu, le));
+                ca += k * step;
+                n = min(step, n - k * step);
             }
+            // 32 consecutive products [qa, qa + 32) touch at most 32 rows
+            // past ca, and every row past ca starts at or after qa: lane L
+            // looks at row ca + 1 + L, the rows starting inside the group
+            // set one bit each, and a product's row is ca plus the bits at
+            // or below its lane
 #pragma unroll
-            for (u32 t = 0; t < RNG_LANE_MAX; t++) jj[t] = m.cur[rr[t]] - offs[rr[t]] + q0 + 32 * t;
+            for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+                const u32 qa = p0 + 32 * t;
+                if (qa < p1) {
+                    const u32 c = ca + 1 + lane;
+                    const u32 st = c < nnz ? (u32)coff[c] : 0xffffffffu;
+                    const u32 bit = st - qa < 32u ? 1u << (st - qa) : 0u;
+                    const u32 mask = __reduce_or_sync(0xffffffffu, bit);
+                    const u32 cc = ca + (u32)__popc(mask & ((2u << lane) - 1u));
+                    rr[t] = crow[cc];
+                    jj[t] = m.cur[rr[t]] + (qa + lane - coff[cc]);
+                    ca += (u32)__popc(mask);
+                }
+            }
 #pragma unroll
             for (u32 t = 0; t < RNG_LANE_MAX; t++) {
                 const u32 q = q0 + 32 * t;
@@ -468,8 +498,8 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     // (issued before the piece was generated) is waited for only now; the
     // scan's barriers make it visible
     if (tid == 0) *s_out = claim_r + written;
-    u64 total;
-    u64 wbase = block_exclusive_scan(lane == 0 ? wcount : 0u, total, ws);
+    u64 nout;
+    u64 wbase = block_exclusive_scan(lane == 0 ? wcount : 0u, nout, ws);
     wbase = __shfl_sync(0xffffffffu, wbase, 0);
     const u64 out = *s_out;
     u32 before = 0;
@@ -484,8 +514,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
         }
         before += (u32)__popc(nzmask[t]);
     }
-    __syncthreads();
-    return total;
+    return nout;
 }
 
 // sum of all products of a single-monomial piece with more than RNG_CHUNK
@@ -602,19 +631,24 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
                 const u64 ar = A[r];
                 const u32 e = rhi_k > ar ? gallop_up(m.Bs, cg, m.cur[r], rhi_k - ar) : m.cur[r];
                 jh[r - r0] = e;
-                mine += e - m.cur[r];
+                mine += row_counts(e - m.cur[r]);
             }
-            u64 O;
-            block_exclusive_scan(mine, O, ws);
+            u64 tot;
+            const u64 base = block_exclusive_scan(mine, tot, ws);
+            const u64 O = (u32)tot;
             // claim the range's output space (at most O terms); only thread
             // 0 holds the base, and waits for it when a piece publishes it
             u64 claim_r = 0;
             if (tid == 0) claim_r = atomicAdd(a.bump, O);
             u64 written = 0;
             if (O <= RNG_CHUNK) {
-                if (O) written = rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, rlo_k, rhi_k, claim_r, 0, &claim, ws);
+                if (O) {
+                    piece_offsets(m, r0, r1, jh, base, tot);
+                    written = rng_piece(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
+                }
+                // own rows only: other threads read these cursors after the
+                // next scan
                 for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
-                __syncthreads();
             } else {
                 // bisect by key: pieces [plo, phi) with at most RNG_CHUNK
                 // products, or a single monomial
@@ -627,14 +661,16 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
                             const u64 ar = A[r];
                             const u32 e = phi > ar ? gallop_up(m.Bs, cg, m.cur[r], phi - ar) : m.cur[r];
                             jh[r - r0] = e;
-                            cnt_mine += e - m.cur[r];
+                            cnt_mine += row_counts(e - m.cur[r]);
                         }
-                        u64 PO;
-                        block_exclusive_scan(cnt_mine, PO, ws);
+                        u64 ptot;
+                        const u64 pbase = block_exclusive_scan(cnt_mine, ptot, ws);
+                        const u64 PO = (u32)ptot;
                         if (PO <= RNG_CHUNK) {
-                            if (PO)
-                                written += rng_piece(a, d, m, A, Ac, Bc, cf, r0, r1, jh, plo, phi, claim_r, written,
-                                                     &claim, ws);
+                            if (PO) {
+                                piece_offsets(m, r0, r1, jh, pbase, ptot);
+                                written += rng_piece(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
+                            }
                             break;
                         }
                         if (phi - plo == 1) {
@@ -644,7 +680,6 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
                         phi = plo + (phi - plo) / 2;
                     }
                     for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
-                    __syncthreads();
                     plo = phi;
                 }
             }
