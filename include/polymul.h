@@ -54,6 +54,7 @@ extern "C" {
 #define PM_ENOMEM        -5  /* device scratch allocation failed                */
 #define PM_ETIMEOUT      -6  /* a bounded device wait gave up                   */
 #define PM_ECUDA         -7  /* a CUDA runtime call failed                      */
+#define PM_EPLAN         -8  /* a plan's inputs no longer match it (pm_plan_*)  */
 
 /* ---- types ---------------------------------------------------------------- */
 
@@ -118,7 +119,10 @@ typedef struct pm_stats {
     uint32_t refine_rounds;    /* partition refinement rounds                      */
     uint32_t kernel_launches;  /* kernels launched by the call                     */
     uint32_t host_syncs;       /* stream synchronisations by the call              */
-    float ms_range_kernel;     /* device time of the accumulate kernel (ms)        */
+    float ms_range_kernel;     /* device time of the accumulate kernel alone: one
+                                  launch of k_direct or k_range_sort (ms)         */
+    float ms_range_step;       /* device time of the range step: windows,
+                                  FindEdge and the accumulate kernel (ms)         */
 } pm_stats;
 
 /* ---- entry points ---------------------------------------------------------- */
@@ -156,6 +160,51 @@ int pm_unpack(const pm_packing *pk, const uint64_t *keys, uint64_t n, uint32_t *
 /* Pack n exponent vectors (device, n x nvars uint32) into keys (device).
  * Fails with PM_EEXP_OVERFLOW if an exponent reaches its guard bit. */
 int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, uint64_t *keys, void *stream);
+
+/* ---- plans: one product, repeated, as a CUDA graph ---------------------------
+ *
+ * pm_polymul reads a small status block on the host twice per call (input
+ * maxima; canonical operand sizes, maxima and extreme keys) and once for
+ * the result size, and launches about thirty kernels, so for products of a
+ * few hundred microseconds the host's launches and waits are a large part
+ * of the call.  A plan runs the product once (filling h, exactly like
+ * pm_polymul), records the two status blocks, and captures the whole device
+ * path -- packing, canonical operands, groups, windows, FindEdge,
+ * accumulation, compaction -- into one CUDA graph.  pm_plan_run replays it:
+ * every kernel runs again on the current contents of f's and g's buffers
+ * (only the host decisions are reused), with no host synchronisation.
+ *
+ * Every host decision of the call is a function of the two status blocks,
+ * so a replay is exact whenever the blocks it computes equal the recorded
+ * ones; on the device, check kernels compare them and on any difference the
+ * kernels that index by data return at entry and pm_plan_finish reports
+ * PM_EPLAN (the inputs' exponent maxima, canonical sizes or extreme
+ * monomials changed: re-create the plan, or call pm_polymul).  Coefficients
+ * may change freely (int64 kind: up to the recorded largest magnitudes),
+ * and so may monomials that keep those statistics.
+ * Products that take the sort strategy (whose partition refinement reads
+ * counts on the host) are not captured: their plan runs plain pm_polymul
+ * calls (pm_plan_captured returns 0).
+ *
+ * The pointers in f, g and h are kept by the plan: their buffers must stay
+ * allocated and unmoved until pm_plan_destroy.  Scratch memory lives in the
+ * graph's allocation nodes.  A plan may be run on any stream; runs of one
+ * plan must not overlap. */
+typedef struct pm_plan pm_plan;
+
+/* Runs h = f * g once (all pm_polymul errors apply, and fail the plan) and
+ * captures the graph.  *plan receives the handle. */
+int pm_plan_create(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                   pm_terms_out *h, const pm_options *opt, pm_plan **plan, void *stream);
+/* Enqueue one replay on `stream` (asynchronous; h's buffers are rewritten). */
+int pm_plan_run(pm_plan *plan, void *stream);
+/* Wait for the last replay on `stream`; *n_out = its result size.  Returns
+ * PM_OK, PM_EPLAN (inputs no longer match: h holds no result),
+ * PM_ECAPACITY (*n_out > h->cap: nothing was written) or PM_ECUDA. */
+int pm_plan_finish(pm_plan *plan, uint64_t *n_out, void *stream);
+/* 1 if the plan replays a captured graph, 0 if it runs plain calls. */
+int pm_plan_captured(const pm_plan *plan);
+void pm_plan_destroy(pm_plan *plan);
 
 /* ---- autotuning ---------------------------------------------------------------
  *

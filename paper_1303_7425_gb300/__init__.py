@@ -8,6 +8,7 @@ missing.
 
 from ._native import (  # noqa: F401
     BatchPlan,
+    Plan,
     autotune,
     batch_autotune,
     Server,
@@ -24,4 +25,4 @@ from ._native import (  # noqa: F401
     unpack,
 )
 
-__all__ = ["BatchPlan", "autotune", "batch_autotune", "Server", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["BatchPlan", "Plan", "autotune", "batch_autotune", "Server", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

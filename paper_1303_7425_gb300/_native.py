@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpolymul.so")
 
 PM_MAX_VARS = 16
 PM_OK, PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND = 0, -1, -2, -3
-PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA = -4, -5, -6, -7
+PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA, PM_EPLAN = -4, -5, -6, -7, -8
 KIND = {"m61": 0, "i64": 1}
 STRATEGY = {"auto": 0, "direct": 1, "sort": 2}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
@@ -47,7 +47,7 @@ class pm_stats(C.Structure):
                 ("n_out", C.c_uint64), ("n_ranges", C.c_uint64), ("box", C.c_uint64),
                 ("strategy", C.c_int32), ("refine_rounds", C.c_uint32),
                 ("kernel_launches", C.c_uint32), ("host_syncs", C.c_uint32),
-                ("ms_range_kernel", C.c_float)]
+                ("ms_range_kernel", C.c_float), ("ms_range_step", C.c_float)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -68,6 +68,7 @@ SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_autotune", 
            "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_batch_workspace",
            "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_progress",
            "pm_server_state", "pm_server_destroy", "pm_polymul_noalloc",
+           "pm_plan_create", "pm_plan_run", "pm_plan_finish", "pm_plan_captured", "pm_plan_destroy",
            "pm_strerror", "pm_version", "pm_probe_mac")
 
 _lib = None
@@ -202,6 +203,83 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
         raise err
     n = int(h.n)
     return Product(keys[:n], coefs[:n], n, st.as_dict())
+
+
+def _plan_lib():
+    L = lib()
+    if not getattr(L, "_plan_ready", False):
+        P = C.POINTER
+        L.pm_plan_create.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), P(pm_terms_out),
+                                     P(pm_options), P(C.c_void_p), C.c_void_p]
+        L.pm_plan_create.restype = C.c_int
+        L.pm_plan_run.argtypes = [C.c_void_p, C.c_void_p]
+        L.pm_plan_run.restype = C.c_int
+        L.pm_plan_finish.argtypes = [C.c_void_p, P(C.c_uint64), C.c_void_p]
+        L.pm_plan_finish.restype = C.c_int
+        L.pm_plan_captured.argtypes = [C.c_void_p]
+        L.pm_plan_captured.restype = C.c_int
+        L.pm_plan_destroy.argtypes = [C.c_void_p]
+        L.pm_plan_destroy.restype = None
+        L._plan_ready = True
+    return L
+
+
+class Plan:
+    """One product, repeated: pm_plan_* (a CUDA graph of the whole device path).
+
+    Creating the plan computes the product once into ``out`` (keys, coefs
+    tensors; their length is the capacity).  ``run()`` enqueues a replay on
+    the current contents of the input tensors, ``finish()`` waits and returns
+    the result size (raises PolymulError with PM_EPLAN when the inputs no
+    longer match the plan).  The tensors must stay alive and unmoved while
+    the plan exists."""
+
+    def __init__(self, field_bits, f_exps, f_coefs, g_exps, g_coefs, out, kind: str = "m61",
+                 strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
+                 accumulator: str = "auto", stream=None):
+        _check_cuda(f_exps, f_coefs, g_exps, g_coefs, out[0], out[1])
+        self._keep = (f_exps, f_coefs, g_exps, g_coefs, out)
+        self.pk = packing(field_bits)
+        self.f = _terms_in(f_exps, f_coefs)
+        self.g = _terms_in(g_exps, g_coefs)
+        self.h = pm_terms_out()
+        self.h.keys = out[0].data_ptr()
+        self.h.coefs = out[1].data_ptr()
+        self.h.cap = int(out[0].shape[0])
+        self.o = options(strategy, slots, chunk, ranges_per_sm, accumulator)
+        self.handle = C.c_void_p()
+        L = _plan_lib()
+        rc = L.pm_plan_create(C.byref(self.pk), KIND[kind], C.byref(self.f), C.byref(self.g), C.byref(self.h),
+                              C.byref(self.o), C.byref(self.handle), _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_plan_create")
+        self.n = int(self.h.n)
+        self.captured = bool(L.pm_plan_captured(self.handle))
+
+    def run(self, stream=None):
+        rc = _plan_lib().pm_plan_run(self.handle, _stream_handle(stream))
+        if rc != PM_OK:
+            raise PolymulError(rc, "pm_plan_run")
+
+    def finish(self, stream=None) -> int:
+        n = C.c_uint64(0)
+        rc = _plan_lib().pm_plan_finish(self.handle, C.byref(n), _stream_handle(stream))
+        if rc != PM_OK:
+            err = PolymulError(rc, "pm_plan_finish")
+            err.needed = int(n.value)
+            raise err
+        return int(n.value)
+
+    def close(self):
+        if self.handle:
+            _plan_lib().pm_plan_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def unpack(field_bits: Sequence[int], keys, stream=None):

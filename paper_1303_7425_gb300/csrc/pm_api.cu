@@ -4,8 +4,10 @@
 // K-b output ranges with balanced operation counts, K-c/K-d one CTA per range,
 // K-e concatenation.  The host only reads sizes and status words between
 // steps; every array the product touches is processed by the kernels.
+#include <cstddef>
 #include <cstring>
 #include <mutex>
+#include <new>
 
 #include "pm_direct.cuh"
 #include "pm_pack.cuh"
@@ -107,6 +109,69 @@ static void read_small(Ctx &c, Small &h, const Small *d)
     c.sync();
 }
 
+// ---------------------------------------------------------------------------
+// Plans (pm_plan_*): a product whose host decisions -- layout, operand
+// sizes, partition sizes, strategy -- are recorded once and whose whole
+// device path is then captured into one CUDA graph.  Every host decision
+// of the call is a function of the small block read at its two host syncs,
+// so a replay is exact whenever the small block it computes equals the
+// recorded one; check kernels compare the two and, on any difference, set
+// a flag at which the kernels that index by data return at entry.
+// ---------------------------------------------------------------------------
+
+constexpr u32 PLAN_MISMATCH = 1u, PLAN_CAPACITY = 2u;
+
+struct PlanRec {
+    enum Mode { DISCOVER, CAPTURE } mode = DISCOVER;
+    Small snap[2];
+    int nsnap = 0, ncap = 0;
+    bool direct = false;      // the recorded call took the direct strategy
+    Small *d_small = nullptr;  // the call's small block (plan-owned, persists)
+    Small *d_snap = nullptr;   // device copies of snap[]
+    u32 *d_flag = nullptr;     // PLAN_* bits of the last replay
+    u64 *d_nout = nullptr;     // result size of the last replay
+};
+
+// Every word must be equal except the largest coefficient magnitudes
+// (int64 kind; words [ma, ma + 4)), which may shrink: the int128 bound rule
+// that passed for the recorded ones then holds too.
+__global__ void k_plan_check(const u32 *__restrict__ cur, const u32 *__restrict__ rec, u32 words, u32 ma,
+                             u32 *flag)
+{
+    u32 diff = 0;
+    for (u32 k = threadIdx.x; k < words; k += blockDim.x)
+        if (k < ma || k >= ma + 4) diff |= cur[k] ^ rec[k];
+    if (threadIdx.x < 2) {
+        const u64 c = (u64)cur[ma + 2 * threadIdx.x] | ((u64)cur[ma + 2 * threadIdx.x + 1] << 32);
+        const u64 r = (u64)rec[ma + 2 * threadIdx.x] | ((u64)rec[ma + 2 * threadIdx.x + 1] << 32);
+        if (c > r) diff = 1;
+    }
+    if (__syncthreads_or(diff != 0) && threadIdx.x == 0) atomicOr(flag, PLAN_MISMATCH);
+}
+
+// the small block after a step: read it (plain call; a plan's first call
+// also records it), or, while a plan is captured, take the recorded one and
+// enqueue the comparison with what the replay computes
+static void fetch_small(Ctx &c, Small &h, const Small *d, PlanRec *rec)
+{
+    if (!rec || rec->mode == PlanRec::DISCOVER) {
+        read_small(c, h, d);
+        if (rec) {
+            if (rec->nsnap >= 2) throw Error(PM_ECUDA, "plan: unexpected host sync");
+            rec->snap[rec->nsnap++] = h;
+        }
+        return;
+    }
+    if (rec->ncap >= rec->nsnap) throw Error(PM_ECUDA, "plan: capture diverged from the recorded call");
+    h = rec->snap[rec->ncap];
+    static_assert(sizeof(Small) % 4 == 0, "small block in words");
+    static_assert(offsetof(Small, maxabs_g) == offsetof(Small, maxabs_f) + 8, "maxabs words adjacent");
+    k_plan_check<<<1, 128, 0, c.s>>>((const u32 *)d, (const u32 *)(rec->d_snap + rec->ncap), sizeof(Small) / 4,
+                                     (u32)(offsetof(Small, maxabs_f) / 4), rec->d_flag);
+    PM_LAUNCHED(c);
+    rec->ncap++;
+}
+
 static u64 host_rank(const Layout &L, u64 key)
 {
     u64 r = 0;
@@ -118,8 +183,14 @@ static u64 host_rank(const Layout &L, u64 key)
 __global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__restrict__ scoef,
                                  const u64 *__restrict__ base, u64 base0, const u64 *__restrict__ foff,
                                  const u64 *__restrict__ ucount, u32 nslices, u32 words, u64 *__restrict__ hkey,
-                                 u64 *__restrict__ hcoef)
+                                 u64 *__restrict__ hcoef, u64 cap, u32 *plan_flag)
 {
+    // foff[nslices] is the result size: nothing is written past the
+    // caller's capacity (a replayed plan reports it through plan_flag)
+    if (foff[nslices] > cap) {
+        if (plan_flag && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(plan_flag, PLAN_CAPACITY);
+        return;
+    }
     for (u32 k = blockIdx.x; k < nslices; k += gridDim.x) {
         const u64 src = base[k] - base0, dst = foff[k], n = ucount[k];
         for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
@@ -135,8 +206,11 @@ __global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__rest
 }
 
 static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, const pm_terms_in *g,
-                        pm_terms_out *h, const pm_options *opt, pm_stats *st, cudaStream_t stream)
+                        pm_terms_out *h, const pm_options *opt, pm_stats *st, cudaStream_t stream,
+                        PlanRec *rec = nullptr)
 {
+    const bool capture = rec && rec->mode == PlanRec::CAPTURE;
+    const u32 *abort = capture ? rec->d_flag : nullptr;
     validate_packing(pk);
     if (kind != PM_COEF_M61 && kind != PM_COEF_I64_ACC128) throw Error(PM_EINVAL, "bad coefficient kind");
     validate_terms(f);
@@ -157,8 +231,9 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     device_setup(c);
     Scratch S(stream);
     Small hs;
-    Small *ds = S.get<Small>(1);
+    Small *ds = rec ? rec->d_small : S.get<Small>(1);
     PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
+    if (capture) PM_CUDA(cudaMemsetAsync(rec->d_flag, 0, sizeof(u32), c.s));
     auto finish = [&](u64 n_out) {
         h->n = n_out;
         stats.n_out = n_out;
@@ -174,7 +249,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     Layout L = base_layout(*pk);
     input_maxima(c, *f, L, ds->maxe_f, &ds->status);
     input_maxima(c, *g, L, ds->maxe_g, &ds->status);
-    read_small(c, hs, ds);
+    fetch_small(c, hs, ds, rec);
     if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
     if (f->n == 0 || g->n == 0) return finish(0);
     Layout raw = L;
@@ -196,15 +271,19 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         const u64 box_f = set_box(own_f, hs.maxe_f, zero);
         const u64 box_g = set_box(own_g, hs.maxe_g, zero);
         auto dense_ok = [](u64 box, u64 n) { return box <= (1ull << 26) && box <= 16 * n + 65536; };
-        if (dense_ok(box_f, f->n)) canonicalize_dense(c, S, *f, own_f, box_f, kind, F, &ds->status, &ds->count_f);
-        else canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
-        if (dense_ok(box_g, g->n)) canonicalize_dense(c, S, *g, own_g, box_g, kind, G, &ds->status, &ds->count_g);
-        else canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
+        if (dense_ok(box_f, f->n))
+            canonicalize_dense(c, S, *f, own_f, box_f, kind, F, &ds->status, &ds->count_f, abort);
+        else
+            canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
+        if (dense_ok(box_g, g->n))
+            canonicalize_dense(c, S, *g, own_g, box_g, kind, G, &ds->status, &ds->count_g, abort);
+        else
+            canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
     }
     PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * 2 * PM_MAX_VARS, c.s));
     operand_stats(c, F, f->n, &ds->count_f, L, kind, ds->maxe_f, &ds->maxabs_f, ds->fl_f);
     operand_stats(c, G, g->n, &ds->count_g, L, kind, ds->maxe_g, &ds->maxabs_g, ds->fl_g);
-    read_small(c, hs, ds);
+    fetch_small(c, hs, ds, rec);
     if (hs.status & ST_COEF_BOUND) throw Error(PM_ECOEF_BOUND, "repeated input monomial leaves int64");
     F.n = hs.count_f;
     G.n = hs.count_g;
@@ -239,15 +318,26 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (strategy == PM_STRATEGY_DIRECT && box >= (1ull << 40))
         throw Error(PM_EINVAL, "exponent box too large for the direct strategy");
     stats.strategy = strategy;
+    if (rec) rec->direct = strategy == PM_STRATEGY_DIRECT;
+    // the sort strategy's partition refinement reads counts on the host
+    if (capture && strategy != PM_STRATEGY_DIRECT) throw Error(PM_ECUDA, "plan: only the direct path is captured");
 
     u64 *okey, *ocoef, *ucount, *foff, *slice_base;
     u64 slice_base0;
     u32 nslices;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (st) {
-        PM_CUDA(cudaEventCreate(&e0));
-        PM_CUDA(cudaEventCreate(&e1));
-    }
+    // timing events (only when stats are asked for), destroyed on every
+    // exit path
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    if (st)
+        for (cudaEvent_t &x : ev.e) PM_CUDA(cudaEventCreate(&x));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], k0 = ev.e[2], k1 = ev.e[3];
 
     if (strategy == PM_STRATEGY_DIRECT) {
         // K-b: ranks, grid sample, groups (no host sync)
@@ -284,8 +374,9 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         a.ocoef = ocoef;
         a.ucount = ucount;
         a.L = L;
+        a.abort = abort;
         if (st) PM_CUDA(cudaEventRecord(e0, c.s));
-        launch_direct(c, S, a, slots, kind, o.accumulator, end);
+        launch_direct(c, S, a, slots, kind, o.accumulator, end, k0, k1);
         if (st) PM_CUDA(cudaEventRecord(e1, c.s));
         stats.n_ranges = Gn;
         slice_base = const_cast<u64 *>(gb);
@@ -326,7 +417,9 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         a.L = L;
         a.status = &ds->status;
         if (st) PM_CUDA(cudaEventRecord(e0, c.s));
+        if (st) PM_CUDA(cudaEventRecord(k0, c.s));
         if (R.n) launch_range_sort(c, a, chunk, kind, R.n);
+        if (st) PM_CUDA(cudaEventRecord(k1, c.s));
         if (st) PM_CUDA(cudaEventRecord(e1, c.s));
         slice_base = R.boff;
         slice_base0 = 0;
@@ -336,14 +429,25 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     // K-e: concatenate the slices in ascending order                  [sync 3]
     foff = S.get<u64>(nslices + 1);
     scan_exclusive_u64(c, S, ucount, foff, nslices);
+    if (capture) {
+        // no host read: the size goes to the plan, the capacity check to
+        // the compaction kernel
+        PM_CUDA(cudaMemcpyAsync(rec->d_nout, foff + nslices, sizeof(u64), cudaMemcpyDeviceToDevice, c.s));
+        if (nslices) {
+            unsigned grid = nslices < 65535u ? nslices : 65535u;
+            k_compact_slices<<<grid, 256, 0, c.s>>>(okey, ocoef, slice_base, slice_base0, foff, ucount, nslices, words,
+                                                    (u64 *)h->keys, (u64 *)h->coefs, h->cap, rec->d_flag);
+            PM_LAUNCHED(c);
+        }
+        return PM_OK;
+    }
     u64 n_out = 0;
     PM_CUDA(cudaMemcpyAsync(&n_out, foff + nslices, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
     PM_CUDA(cudaMemcpyAsync(&hs.status, &ds->status, sizeof(u32), cudaMemcpyDeviceToHost, c.s));
     c.sync();
     if (st) {
-        PM_CUDA(cudaEventElapsedTime(&stats.ms_range_kernel, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        PM_CUDA(cudaEventElapsedTime(&stats.ms_range_step, e0, e1));
+        PM_CUDA(cudaEventElapsedTime(&stats.ms_range_kernel, k0, k1));
     }
     if (hs.status & ST_INTERNAL) throw Error(PM_ECUDA, "internal consistency check failed");
     stats.n_out = n_out;
@@ -359,7 +463,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (nslices && n_out) {
         unsigned grid = nslices < 65535u ? nslices : 65535u;
         k_compact_slices<<<grid, 256, 0, c.s>>>(okey, ocoef, slice_base, slice_base0, foff, ucount, nslices, words,
-                                                (u64 *)h->keys, (u64 *)h->coefs);
+                                                (u64 *)h->keys, (u64 *)h->coefs, h->cap, nullptr);
         PM_LAUNCHED(c);
     }
     return finish(n_out);
@@ -456,6 +560,161 @@ extern "C" int pm_pack(const pm_packing *pk, const uint32_t *exps, uint64_t n, u
     });
 }
 
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+
+struct pm_plan {
+    PlanRec rec;
+    pm_packing pk;
+    int kind;
+    pm_terms_in f, g;
+    pm_terms_out h;
+    pm_options opt;
+    bool has_opt = false;
+    bool captured = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    u32 *host = nullptr;   // pinned: flag, status, n_out (2 words)
+    int last_rc = PM_OK;   // plain (not captured) plans: result of the last run
+    u64 last_n = 0;
+};
+
+static void plan_free(pm_plan *p)
+{
+    if (!p) return;
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->rec.d_small) cudaFree(p->rec.d_small);
+    if (p->host) cudaFreeHost(p->host);
+    delete p;
+}
+
+extern "C" int pm_plan_create(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                              pm_terms_out *h, const pm_options *opt, pm_plan **plan, void *stream)
+{
+    if (!plan) return PM_EINVAL;
+    *plan = nullptr;
+    pm_plan *p = new (std::nothrow) pm_plan;
+    if (!p) return PM_ENOMEM;
+    int rc = guarded([&] {
+        if (!pk || !f || !g || !h) throw Error(PM_EINVAL, "null argument");
+        p->pk = *pk;
+        p->kind = coef_kind;
+        p->f = *f;
+        p->g = *g;
+        p->h = *h;
+        p->has_opt = opt != nullptr;
+        if (opt) p->opt = *opt;
+        // one device block: the call's small block, the two recorded
+        // snapshots, the flag and the result size
+        const size_t bytes = 3 * sizeof(Small) + 16;
+        void *d = nullptr;
+        if (cudaMalloc(&d, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(PM_ENOMEM, "plan block");
+        }
+        p->rec.d_small = (Small *)d;
+        p->rec.d_snap = p->rec.d_small + 1;
+        p->rec.d_flag = (u32 *)(p->rec.d_small + 3);
+        p->rec.d_nout = (u64 *)((char *)d + 3 * sizeof(Small) + 8);
+        PM_CUDA(cudaMemset(d, 0, bytes));
+        PM_CUDA(cudaMallocHost((void **)&p->host, 16));
+        // the recorded call: a plain product that also fills h
+        cudaStream_t s = (cudaStream_t)stream;
+        p->rec.mode = PlanRec::DISCOVER;
+        int r = polymul_impl(pk, coef_kind, f, g, h, opt, nullptr, s, &p->rec);
+        if (r != PM_OK) return r;
+        p->last_n = h->n;
+        if (!p->rec.direct || p->rec.nsnap != 2) return PM_OK;  // runs as plain calls
+        PM_CUDA(cudaMemcpy(p->rec.d_snap, p->rec.snap, 2 * sizeof(Small), cudaMemcpyHostToDevice));
+        // capture on a stream of our own (the caller's may be the legacy
+        // default stream, which cannot be captured)
+        cudaStream_t cs;
+        PM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        p->rec.mode = PlanRec::CAPTURE;
+        p->rec.ncap = 0;
+        pm_terms_out hh = *h;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            throw Error(PM_ECUDA, "begin capture");
+        }
+        int crc = PM_OK;
+        try {
+            crc = polymul_impl(pk, coef_kind, f, g, &hh, opt, nullptr, cs, &p->rec);
+        } catch (const Error &err) {
+            crc = err.code;
+        }
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(cs, &graph);
+        cudaStreamDestroy(cs);
+        if (crc != PM_OK || e != cudaSuccess || !graph) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            throw Error(crc != PM_OK ? crc : PM_ECUDA, "capture");
+        }
+        p->graph = graph;
+        PM_CUDA(cudaGraphInstantiate(&p->exec, graph, 0));
+        p->captured = true;
+        return PM_OK;
+    });
+    if (rc != PM_OK) {
+        plan_free(p);
+        return rc;
+    }
+    *plan = p;
+    return PM_OK;
+}
+
+extern "C" int pm_plan_run(pm_plan *p, void *stream)
+{
+    if (!p) return PM_EINVAL;
+    if (p->captured) {
+        cudaError_t e = cudaGraphLaunch(p->exec, (cudaStream_t)stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return PM_ECUDA;
+        }
+        return PM_OK;
+    }
+    // not captured (sort strategy or an empty product): a plain call
+    pm_terms_out hh = p->h;
+    p->last_rc = pm_polymul(&p->pk, p->kind, &p->f, &p->g, &hh, p->has_opt ? &p->opt : nullptr, nullptr, stream);
+    p->last_n = hh.n;
+    return p->last_rc == PM_ECAPACITY ? PM_OK : p->last_rc;
+}
+
+extern "C" int pm_plan_finish(pm_plan *p, uint64_t *n_out, void *stream)
+{
+    if (!p) return PM_EINVAL;
+    if (!p->captured) {
+        if (n_out) *n_out = p->last_n;
+        return p->last_rc;
+    }
+    return guarded([&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        PM_CUDA(cudaMemcpyAsync(p->host, p->rec.d_flag, 4, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaMemcpyAsync(p->host + 1, &p->rec.d_small->status, 4, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaMemcpyAsync(p->host + 2, p->rec.d_nout, 8, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+        const u32 flag = p->host[0], status = p->host[1];
+        u64 n = 0;
+        memcpy(&n, p->host + 2, 8);
+        if (flag & PLAN_MISMATCH) {
+            if (n_out) *n_out = 0;
+            return PM_EPLAN;
+        }
+        if (status & ST_INTERNAL) throw Error(PM_ECUDA, "internal consistency check failed");
+        if (n_out) *n_out = n;
+        return (flag & PLAN_CAPACITY) ? PM_ECAPACITY : PM_OK;
+    });
+}
+
+extern "C" int pm_plan_captured(const pm_plan *p) { return p && p->captured ? 1 : 0; }
+
+extern "C" void pm_plan_destroy(pm_plan *p) { plan_free(p); }
+
 extern "C" const char *pm_strerror(int code)
 {
     switch (code) {
@@ -467,6 +726,7 @@ extern "C" const char *pm_strerror(int code)
     case PM_ENOMEM: return "device memory allocation failed";
     case PM_ETIMEOUT: return "bounded device wait timed out";
     case PM_ECUDA: return "CUDA runtime error";
+    case PM_EPLAN: return "inputs no longer match the plan (re-create it or call pm_polymul)";
     default: return "unknown error";
     }
 }

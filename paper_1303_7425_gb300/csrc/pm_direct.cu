@@ -21,7 +21,8 @@ namespace pm {
 
 constexpr int DT = 1024;          // threads per CTA
 constexpr int DW = DT / 32;       // warps
-constexpr int DROWS = DT;         // rows staged per pass
+constexpr int DRPT = 1;           // rows staged per thread and pass
+constexpr int DROWS = DT * DRPT;  // rows staged per pass
 
 struct DTables {
     u32 *ra;    // (u32) rank of alpha_i
@@ -307,6 +308,12 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const u32 g = blockIdx.x;
     if (g >= a.ngroups) return;
+    // inputs that no longer match a replayed plan could put products
+    // outside the windows; such a replay computes nothing
+    if (a.abort && *a.abort) {
+        if (tid == 0) a.ucount[g] = 0;
+        return;
+    }
     const u64 obase = a.gb[g] - a.lo;
     const u32 nb = a.nb, na = a.na;
     u64 run = 0;
@@ -324,19 +331,30 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         __syncthreads();
 
         for (u32 base = i0; base < i1; base += DROWS) {
-            const u32 i = base + tid;
+            // thread tid stages rows base + tid * DRPT + [0, DRPT)
+            u32 lens[DRPT];
             u64 len = 0;
-            if (i < i1) {
-                const u32 jl = i < i1lo ? Elo[i] : 0u;
-                const u32 jh = i >= i0hi ? Ehi[i] : nb;
-                len = jh - jl;
-                t.ra[tid] = (u32)__ldg(a.A + i);
-                t.ca[tid] = __ldg(a.Ac + i);
-                t.jlo[tid] = jl;
+#pragma unroll
+            for (int k = 0; k < DRPT; k++) {
+                const u32 li = tid * DRPT + k, i = base + li;
+                lens[k] = 0;
+                if (i < i1) {
+                    const u32 jl = i < i1lo ? Elo[i] : 0u;
+                    const u32 jh = i >= i0hi ? Ehi[i] : nb;
+                    lens[k] = jh - jl;
+                    t.ra[li] = (u32)__ldg(a.A + i);
+                    t.ca[li] = __ldg(a.Ac + i);
+                    t.jlo[li] = jl;
+                }
+                len += lens[k];
             }
             u64 total;
-            const u64 ex = block_exclusive_scan(len, total, ws);
-            t.off[tid] = (u32)ex;
+            u64 ex = block_exclusive_scan(len, total, ws);
+#pragma unroll
+            for (int k = 0; k < DRPT; k++) {
+                t.off[tid * DRPT + k] = (u32)ex;
+                ex += lens[k];
+            }
             if (tid == 0) t.off[DROWS] = (u32)total;
             const u32 nrows = min(i1 - base, (u32)DROWS);
             __syncthreads();
@@ -536,7 +554,8 @@ static void set_smem(K kernel, size_t bytes)
 }
 
 
-void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end)
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end,
+                   cudaEvent_t ev_k0, cudaEvent_t ev_k1)
 {
     const u32 G = a.ngroups;
     // window boundaries W (at most G + span / slots + 1 of them)
@@ -577,6 +596,7 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     // accumulate, one CTA per group
     const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
     const size_t bytes = (size_t)slots * acc_bytes(acc) + DTABLE_BYTES;
+    if (ev_k0) PM_CUDA(cudaEventRecord(ev_k0, c.s));
     if (acc == ACC_W64) {
         set_smem(k_direct<ACC_W64>, bytes);
         k_direct<ACC_W64><<<G, DT, bytes, c.s>>>(a, slots);
@@ -588,6 +608,7 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
         k_direct<ACC_I128><<<G, DT, bytes, c.s>>>(a, slots);
     }
     PM_LAUNCHED(c);
+    if (ev_k1) PM_CUDA(cudaEventRecord(ev_k1, c.s));
 }
 
 }  // namespace pm

@@ -23,12 +23,15 @@ struct DirectArgs {
     u64 *okey, *ocoef;   // output scratch
     u64 *ucount;         // terms written per group
     Layout L;
+    const u32 *abort;    // non-zero: a replayed plan's inputs no longer match it (may be null)
 };
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
 u32 direct_max_slots(int kind, u64 min_n, int requested);
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
                    u32 grid_l, u64 products, double slot_cost);
-void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end);
+// ev_k0 / ev_k1 (may be null): events recorded around the accumulate launch
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end,
+                   cudaEvent_t ev_k0 = nullptr, cudaEvent_t ev_k1 = nullptr);
 
 }  // namespace pm

@@ -204,10 +204,12 @@ void canonicalize(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &raw, 
 // ---------------------------------------------------------------------------
 
 __global__ void k_dense_scatter(const u32 *__restrict__ exps, const void *__restrict__ coefs, size_t n, Layout L,
-                                int kind, u64 *__restrict__ sum, u64 *__restrict__ aux)
+                                int kind, u64 *__restrict__ sum, u64 *__restrict__ aux, const u32 *abort)
 {
     size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
+    // a replayed plan whose inputs left the recorded box stops here: the
+    // box below would no longer bound the ranks
+    if (t >= n || (abort && *abort)) return;
     u64 r = 0;
     for (u32 v = 0; v < L.nv; v++) r += (u64)exps[t * L.nv + v] * L.stride[v];
     const u64 c = ((const u64 *)coefs)[t];
@@ -256,14 +258,14 @@ __global__ void k_dense_emit(const u64 *__restrict__ sum, const u64 *__restrict_
 }
 
 void canonicalize_dense(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &own, u64 own_box, int kind,
-                        Operand &op, u32 *d_status, u64 *d_count)
+                        Operand &op, u32 *d_status, u64 *d_count, const u32 *abort)
 {
     op.n = 0;
     const size_t n = in.n;
     u64 *sum = S.get<u64>(own_box), *aux = S.get<u64>(own_box);
     PM_CUDA(cudaMemsetAsync(sum, 0, own_box * 8, c.s));
     PM_CUDA(cudaMemsetAsync(aux, 0, own_box * 8, c.s));
-    k_dense_scatter<<<grid_for(n, 256), 256, 0, c.s>>>(in.exps, in.coefs, n, own, kind, sum, aux);
+    k_dense_scatter<<<grid_for(n, 256), 256, 0, c.s>>>(in.exps, in.coefs, n, own, kind, sum, aux, abort);
     PM_LAUNCHED(c);
     u64 *flag = S.get<u64>(own_box), *pos = S.get<u64>(own_box + 1);
     k_dense_flags<<<grid_for(own_box, 256), 256, 0, c.s>>>(sum, aux, own_box, kind, flag, d_status);

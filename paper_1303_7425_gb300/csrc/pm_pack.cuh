@@ -22,7 +22,8 @@ void canonicalize(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &raw, 
 // Canonical operand by scatter into its own exponent box (own_box slots,
 // strides in `own`): for boxes not much larger than the operand.
 void canonicalize_dense(Ctx &c, Scratch &S, const pm_terms_in &in, const Layout &own, u64 own_box, int kind,
-                        Operand &op, u32 *d_status, u64 *d_count);
+                        Operand &op, u32 *d_status, u64 *d_count,
+                        const u32 *abort = nullptr);
 void operand_stats(Ctx &c, const Operand &op, u64 n_max, const u64 *d_n, const Layout &L, int kind, u32 *d_maxe,
                    u64 *d_maxabs, u64 *d_first_last);
 // rank32 (optional): also store the low 32 bits of each rank
