@@ -89,6 +89,7 @@ static u64 set_box(Layout &L, const u32 *mf, const u32 *mg)
     u64 stride = 1;
     for (int v = (int)L.nv - 1; v >= 0; v--) {
         L.extent[v] = (u64)mf[v] + mg[v] + 1;
+        fastdiv_params(L.extent[v], L.dmag[v], L.dsh[v]);
         L.stride[v] = stride;
         stride *= L.extent[v];
     }

@@ -140,7 +140,37 @@ struct Layout {
     u32 width[PM_MAX_VARS];   // field width incl. guard bit
     u64 stride[PM_MAX_VARS];  // mixed-radix stride of x_v in the rank box
     u64 extent[PM_MAX_VARS];  // rank box extent of x_v
+    // division by extent[v] < 2^32 as a multiply-high and two shifts
+    // (set with the extents, see fastdiv_params)
+    u32 dmag[PM_MAX_VARS];
+    u32 dsh[PM_MAX_VARS];     // sh1 | sh2 << 8
 };
+
+// Division of a 32-bit n by an invariant 1 <= d < 2^32 with one multiply-
+// high (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, Fig. 4.1): with l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, sh1 = min(l, 1), sh2 = max(l - 1, 0),
+// t = mulhi(m, n) and q = (t + ((n - t) >> sh1)) >> sh2 = floor(n / d).
+inline void fastdiv_params(u64 d, u32 &m, u32 &sh)
+{
+    if (d == 0 || d > 0xFFFFFFFFull) {
+        m = 0;
+        sh = 0;
+        return;
+    }
+    u32 l = 0;
+    while ((1ull << l) < d) l++;
+    const unsigned __int128 num = ((unsigned __int128)1 << 32) * (((unsigned __int128)1 << l) - d);
+    m = (u32)(num / d + 1);
+    const u32 sh1 = l < 1 ? l : 1, sh2 = l > 1 ? l - 1 : 0;
+    sh = sh1 | (sh2 << 8);
+}
+
+__device__ __forceinline__ u32 fastdiv(u32 n, u32 m, u32 sh)
+{
+    const u32 t = __umulhi(m, n);
+    return (t + ((n - t) >> (sh & 0xFF))) >> (sh >> 8);
+}
 
 __device__ __forceinline__ u32 key_field(const Layout &L, u64 key, u32 v)
 {
@@ -159,10 +189,12 @@ __device__ __forceinline__ u64 rank_to_key(const Layout &L, u64 rank)
 {
     u64 key = 0;
     if (rank <= 0xFFFFFFFFull) {
+        // extents are below 2^32 (fields of at most 32 bits, guard bit
+        // included), so the fast division applies
         u32 r = (u32)rank;
         for (int v = (int)L.nv - 1; v >= 0; v--) {
-            u32 e = (u32)L.extent[v];
-            u32 q = r / e;
+            const u32 e = (u32)L.extent[v];
+            const u32 q = fastdiv(r, L.dmag[v], L.dsh[v]);
             key |= (u64)(r - q * e) << L.off[v];
             r = q;
         }

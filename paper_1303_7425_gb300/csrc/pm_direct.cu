@@ -24,23 +24,31 @@ constexpr int DW = DT / 32;       // warps
 constexpr int DRPT = 1;           // rows staged per thread and pass
 constexpr int DROWS = DT * DRPT;  // rows staged per pass
 
+// shared-memory row tables of one pass: per staged row a 16-byte record
+// (a_i as two words, rank of alpha_i minus the window start, first column
+// minus the row's offset in the pass), so a lane that moves to the next row
+// reloads its row state with one 16-byte load; plus the offsets
 struct DTables {
-    u32 *ra;    // (u32) rank of alpha_i
-    u64 *ca;    // a_i
-    u32 *jlo;   // first column in the window
-    u32 *off;   // exclusive prefix of row spans (DROWS + 1)
+    uint4 *rec;  // DROWS records
+    u32 *off;    // exclusive prefix of row spans (DROWS + 1)
 };
 
-constexpr size_t DTABLE_BYTES = (size_t)DROWS * (4 + 8 + 4) + (DROWS + 1) * 4 + 12;
+constexpr size_t DTABLE_BYTES = (size_t)DROWS * 16 + (DROWS + 1) * 4 + 12;
 
 __device__ __forceinline__ DTables carve_dtables(unsigned char *p)
 {
     DTables t;
-    t.ca = (u64 *)p;
-    t.ra = (u32 *)(t.ca + DROWS);
-    t.jlo = t.ra + DROWS;
-    t.off = t.jlo + DROWS;
+    t.rec = (uint4 *)p;
+    t.off = (u32 *)(t.rec + DROWS);
     return t;
+}
+
+// accumulator slots per window: as many as fit beside the tables, a
+// multiple of 1024; a compile-time constant, so the accumulator's parallel
+// arrays sit at fixed offsets from each other
+constexpr u32 acc_stride(u32 bytes_per_slot)
+{
+    return (u32)((227 * 1024 - DTABLE_BYTES - 512) / bytes_per_slot) & ~1023u;
 }
 
 __device__ __forceinline__ u32 d_row_of(const u32 *off, u32 nrows, u32 p)
@@ -182,31 +190,32 @@ struct Stream {
     u64 ca;
 };
 
-__device__ __forceinline__ void stream_load_row(Stream &c, const DTables &t, u32 lo32)
+__device__ __forceinline__ void stream_load_row(Stream &c, const DTables &t)
 {
+    const uint4 q = t.rec[c.r];
+    c.ca = (u64)q.x | ((u64)q.y << 32);
+    c.ra = q.z;
+    c.jbase = q.w;
     c.rend = t.off[c.r + 1];
-    c.jbase = t.jlo[c.r] - t.off[c.r];
-    c.ra = t.ra[c.r] - lo32;
-    c.ca = t.ca[c.r];
 }
 
-__device__ __forceinline__ void stream_init(Stream &c, const DTables &t, u32 nrows, u32 p, u32 end, u32 lo32)
+__device__ __forceinline__ void stream_init(Stream &c, const DTables &t, u32 nrows, u32 p, u32 end)
 {
     c.p = p;
     c.end = end;
     if (p < end) {
         c.r = d_row_of(t.off, nrows, p);
-        stream_load_row(c, t, lo32);
+        stream_load_row(c, t);
     }
 }
 
-__device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t, u32 lo32)
+__device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t)
 {
     if (c.p >= c.rend) {
         do {
             c.r++;
         } while (t.off[c.r + 1] <= c.p);
-        stream_load_row(c, t, lo32);
+        stream_load_row(c, t);
     }
 }
 
@@ -227,15 +236,14 @@ enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2 };
 template <int ACC>
 struct Acc {
     static constexpr u32 bytes = ACC == ACC_W64 ? 12 : 16;
+    static constexpr u32 slots = acc_stride(bytes);  // array stride (the window may use fewer)
     u64 *w;      // ACC_W64: sums; ACC_I128: lo words [0, slots), hi words [slots, 2 slots)
     u32 *c;      // ACC_W64: wrap counts; ACC_L16: limb counters, limb k at [k * slots, (k+1) * slots)
-    u32 slots;
 
-    __device__ __forceinline__ void carve(unsigned char *p, u32 n)
+    __device__ __forceinline__ void carve(unsigned char *p)
     {
-        slots = n;
         w = (u64 *)p;
-        c = ACC == ACC_W64 ? (u32 *)(w + n) : (u32 *)p;
+        c = ACC == ACC_W64 ? (u32 *)(w + slots) : (u32 *)p;
     }
     __device__ __forceinline__ void zero(u32 s)
     {
@@ -271,6 +279,44 @@ struct Acc {
             atomicAdd(&w[slots + s], phi + (old + plo < old ? 1ull : 0ull));
         }
     }
+    // emission, first pass: the slot's value (residue mod p with v1 = 0, or
+    // the int128 (v0, v1)), left in the slot in a form take() reads back
+    // with fewer loads: a residue as two 32-bit words in the first two
+    // arrays (ACC_L16) or as the whole sum (ACC_W64)
+    __device__ __forceinline__ bool finalize(u32 s, u64 &v0, u64 &v1)
+    {
+        const bool nz = value(s, v0, v1);
+        if (ACC == ACC_W64) {
+            w[s] = v0;
+            c[s] = 0;
+        } else if (ACC == ACC_L16) {
+            c[s] = (u32)v0;
+            c[slots + s] = (u32)(v0 >> 32);
+            c[2 * slots + s] = 0;
+            c[3 * slots + s] = 0;
+        }
+        return nz;
+    }
+    // emission, second pass: the value finalize() left, and the slot cleared
+    // for the next window
+    __device__ __forceinline__ void take(u32 s, u64 &v0, u64 &v1)
+    {
+        if (ACC == ACC_W64) {
+            v0 = w[s];
+            v1 = 0;
+            w[s] = 0;
+        } else if (ACC == ACC_L16) {
+            v0 = (u64)c[s] | ((u64)c[slots + s] << 32);
+            v1 = 0;
+            c[s] = 0;
+            c[slots + s] = 0;
+        } else {
+            v0 = w[s];
+            v1 = w[slots + s];
+            w[s] = 0;
+            w[slots + s] = 0;
+        }
+    }
     // the slot's value: residue mod p (v1 = 0), or the int128 (v0, v1)
     __device__ __forceinline__ bool value(u32 s, u64 &v0, u64 &v1) const
     {
@@ -303,8 +349,8 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
     Acc<ACC> acc;
-    acc.carve(smem, slots);
-    DTables t = carve_dtables(smem + (size_t)slots * Acc<ACC>::bytes);
+    acc.carve(smem);
+    DTables t = carve_dtables(smem + (size_t)Acc<ACC>::slots * Acc<ACC>::bytes);
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const u32 g = blockIdx.x;
     if (g >= a.ngroups) return;
@@ -317,6 +363,9 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
     const u64 obase = a.gb[g] - a.lo;
     const u32 nb = a.nb, na = a.na;
     u64 run = 0;
+    // every slot starts at zero; each window's emission clears the slots
+    // it read, so the next window starts from zero again
+    for (u32 x = tid; x < Acc<ACC>::slots; x += DT) acc.zero(x);
 
     for (u64 bw = a.wpos[g], bend = a.wpos[g + 1]; bw < bend; bw++) {
         const u64 lo = a.W[bw], hi = a.W[bw + 1];
@@ -327,24 +376,28 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         const u32 i0 = a.i0s[bw], i1 = a.i1s[bw + 1];
         const u32 i1lo = a.i1s[bw], i0hi = a.i0s[bw + 1];
         const u32 *Elo = a.E + bw * na, *Ehi = Elo + na;
-        for (u32 s = tid; s < span; s += DT) acc.zero(s);
         __syncthreads();
 
         for (u32 base = i0; base < i1; base += DROWS) {
-            // thread tid stages rows base + tid * DRPT + [0, DRPT)
-            u32 lens[DRPT];
+            // thread tid stages rows base + tid * DRPT + [0, DRPT); the
+            // records need the rows' offsets, so they are written after the
+            // scan
+            u32 lens[DRPT], jls[DRPT], ras[DRPT];
+            u64 cas[DRPT];
             u64 len = 0;
 #pragma unroll
             for (int k = 0; k < DRPT; k++) {
-                const u32 li = tid * DRPT + k, i = base + li;
+                const u32 i = base + tid * DRPT + k;
                 lens[k] = 0;
+                jls[k] = 0;
+                ras[k] = 0;
+                cas[k] = 0;
                 if (i < i1) {
-                    const u32 jl = i < i1lo ? Elo[i] : 0u;
+                    jls[k] = i < i1lo ? Elo[i] : 0u;
                     const u32 jh = i >= i0hi ? Ehi[i] : nb;
-                    lens[k] = jh - jl;
-                    t.ra[li] = (u32)__ldg(a.A + i);
-                    t.ca[li] = __ldg(a.Ac + i);
-                    t.jlo[li] = jl;
+                    lens[k] = jh - jls[k];
+                    ras[k] = (u32)__ldg(a.A + i) - (u32)lo;
+                    cas[k] = __ldg(a.Ac + i);
                 }
                 len += lens[k];
             }
@@ -352,7 +405,9 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             u64 ex = block_exclusive_scan(len, total, ws);
 #pragma unroll
             for (int k = 0; k < DRPT; k++) {
-                t.off[tid * DRPT + k] = (u32)ex;
+                const u32 li = tid * DRPT + k;
+                t.off[li] = (u32)ex;
+                t.rec[li] = make_uint4((u32)cas[k], (u32)(cas[k] >> 32), ras[k], jls[k] - (u32)ex);
                 ex += lens[k];
             }
             if (tid == 0) t.off[DROWS] = (u32)total;
@@ -367,22 +422,21 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             const u32 p0 = w * per_warp;
             const u32 p1 = min(p0 + per_warp, tot);
             const u32 pm = min(p0 + per_warp / 2, p1);
-            const u32 lo32 = (u32)lo;
             Stream sa, sb;
-            stream_init(sa, t, nrows, p0 + lane, pm, lo32);
-            stream_init(sb, t, nrows, pm + lane, p1, lo32);
+            stream_init(sa, t, nrows, p0 + lane, pm);
+            stream_init(sb, t, nrows, pm + lane, p1);
             while (sa.p < sa.end || sb.p < sb.end) {
                 const bool va = sa.p < sa.end, vb = sb.p < sb.end;
                 u32 ja = 0, jb = 0, ba = 0, bb = 0;
                 u64 ga = 0, gbv = 0;
                 if (va) {
-                    stream_advance_row(sa, t, lo32);
+                    stream_advance_row(sa, t);
                     ja = sa.jbase + sa.p;
                     ba = __ldg(a.B32 + ja);
                     ga = __ldg(a.Bc + ja);
                 }
                 if (vb) {
-                    stream_advance_row(sb, t, lo32);
+                    stream_advance_row(sb, t);
                     jb = sb.jbase + sb.p;
                     bb = __ldg(a.B32 + jb);
                     gbv = __ldg(a.Bc + jb);
@@ -396,8 +450,9 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         }
 
         // emit the window's non-zero slots in ascending order: warp w owns
-        // the contiguous slots [w * chunk, (w + 1) * chunk); pass 1 counts,
-        // one block scan places the warps, pass 2 writes
+        // the contiguous slots [w * chunk, (w + 1) * chunk); pass 1 computes
+        // the values and counts, one block scan places the warps, pass 2
+        // writes and clears the slots (warp-private, so no barrier between)
         const u32 chunk = ((span + DW - 1) / DW + 31u) & ~31u;
         const u32 s0 = w * chunk, s1 = min(s0 + chunk, span);
         u32 wcount = 0;
@@ -405,7 +460,7 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             const u32 s = sb + lane;
             bool nz = false;
             u64 x0, x1;
-            if (s < s1) nz = acc.value(s, x0, x1);
+            if (s < s1) nz = acc.finalize(s, x0, x1);
             wcount += __popc(__ballot_sync(0xffffffffu, nz));
         }
         u64 wtot;
@@ -414,8 +469,8 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         for (u32 sb = s0; sb < s1; sb += 32) {
             const u32 s = sb + lane;
             u64 v0 = 0, v1 = 0;
-            bool nz = false;
-            if (s < s1) nz = acc.value(s, v0, v1);
+            if (s < s1) acc.take(s, v0, v1);
+            const bool nz = (v0 | v1) != 0;
             const u32 bal = __ballot_sync(0xffffffffu, nz);
             if (nz) {
                 const u64 d = put + __popc(bal & ((1u << lane) - 1u));
@@ -537,14 +592,15 @@ static u32 acc_bytes(int acc) { return acc == ACC_W64 ? 12 : 16; }
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested)
 {
-    return (size_t)slots * acc_bytes(acc_policy(kind, min_n, requested)) + DTABLE_BYTES;
+    (void)slots;  // the accumulator arrays always take their full stride
+    const u32 b = acc_bytes(acc_policy(kind, min_n, requested));
+    return (size_t)acc_stride(b) * b + DTABLE_BYTES;
 }
 
 u32 direct_max_slots(int kind, u64 min_n, int requested)
 {
     // 227 KB of opt-in shared memory per CTA, minus tables and static use
-    size_t avail = 227 * 1024 - DTABLE_BYTES - 512;
-    return (u32)(avail / acc_bytes(acc_policy(kind, min_n, requested))) & ~1023u;
+    return acc_stride(acc_bytes(acc_policy(kind, min_n, requested)));
 }
 
 template <class K>
@@ -595,7 +651,7 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 
     // accumulate, one CTA per group
     const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
-    const size_t bytes = (size_t)slots * acc_bytes(acc) + DTABLE_BYTES;
+    const size_t bytes = (size_t)acc_stride(acc_bytes(acc)) * acc_bytes(acc) + DTABLE_BYTES;
     if (ev_k0) PM_CUDA(cudaEventRecord(ev_k0, c.s));
     if (acc == ACC_W64) {
         set_smem(k_direct<ACC_W64>, bytes);

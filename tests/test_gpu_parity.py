@@ -211,6 +211,25 @@ def test_packing_extremes(bits, hi):
         assert_same(gpu, ref, bits)
 
 
+@pytest.mark.parametrize("bits,lims", [([32], [(1 << 30) - 1]),            # extent 2^31 - 1
+                                       ([16, 16], [(1 << 14) - 1, 3]),       # extents 2^15 - 1 and 7
+                                       ([8, 8, 8, 8], [2, 63, 1, 40])])      # small odd extents
+def test_direct_rank_decoding_extents(bits, lims):
+    """Forced direct strategy on boxes whose extents run from 3 to 2^31 - 1:
+    every output key is rebuilt from its rank by division by the extents."""
+    nv = len(bits)
+    st = polygen.Stream(17, nv)
+    fe = np.stack([st.below(l + 1, 40).astype(np.uint32) for l in lims], axis=1)
+    ge = np.stack([st.below(l + 1, 30).astype(np.uint32) for l in lims], axis=1)
+    fe[0] = lims
+    ge[0] = lims                                        # the largest exponent sum is reached
+    fc, gc = st.coef_m61(40), st.coef_m61(30)
+    ref = oracle.mul(nv, bits, "m61", fe, fc, ge, gc)
+    gpu = run_gpu(bits, "m61", fe, fc, ge, gc, strategy="direct")
+    assert gpu[2]["strategy"] == "direct"
+    assert_same(gpu, ref, bits)
+
+
 def test_int128_near_bound():
     a, b = -2**63, 2**63 - 1
     fe = np.array([[0], [1]], np.uint32)
