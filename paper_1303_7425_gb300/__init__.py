@@ -13,6 +13,7 @@ from ._native import (  # noqa: F401
     batch_autotune,
     Server,
     batch_polymul,
+    batch_workspace,
     PolymulError,
     Product,
     SYMBOLS,
@@ -25,4 +26,4 @@ from ._native import (  # noqa: F401
     unpack,
 )
 
-__all__ = ["BatchPlan", "Plan", "autotune", "batch_autotune", "Server", "batch_polymul", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]
+__all__ = ["BatchPlan", "Plan", "autotune", "batch_autotune", "Server", "batch_polymul", "batch_workspace", "polymul", "polymul_noalloc", "unpack", "pack", "out_bound", "probe_mac", "PolymulError", "Product", "lib", "SYMBOLS"]

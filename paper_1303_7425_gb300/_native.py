@@ -39,7 +39,8 @@ class pm_terms_out(C.Structure):
 
 class pm_options(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("slots", C.c_uint32), ("chunk", C.c_uint32),
-                ("ranges_per_sm", C.c_uint32), ("accumulator", C.c_int32)]
+                ("ranges_per_sm", C.c_uint32), ("accumulator", C.c_int32), ("cost_row", C.c_uint32),
+                ("cost_window", C.c_uint32)]
 
 
 class pm_stats(C.Structure):
@@ -113,13 +114,15 @@ def packing(field_bits: Sequence[int]) -> pm_packing:
 
 
 def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
-            accumulator: str = "auto") -> pm_options:
+            accumulator: str = "auto", cost_row: int = 0, cost_window: int = 0) -> pm_options:
     o = pm_options()
     o.strategy = STRATEGY[strategy]
     o.slots = slots
     o.chunk = chunk
     o.ranges_per_sm = ranges_per_sm
     o.accumulator = ACCUMULATOR[accumulator]
+    o.cost_row = cost_row
+    o.cost_window = cost_window
     return o
 
 
@@ -168,7 +171,7 @@ def out_bound(field_bits, f_exps, g_exps, stream=None) -> int:
 
 def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61",
             strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
-            accumulator: str = "auto", out=None, stream=None) -> Product:
+            accumulator: str = "auto", out=None, stream=None, cost_row: int = 0, cost_window: int = 0) -> Product:
     """h = f * g on the current CUDA device.
 
     f_exps/g_exps: (n, nvars) int32/uint32 CUDA tensors; f_coefs/g_coefs: (n,)
@@ -194,7 +197,7 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
     h.coefs = coefs.data_ptr()
     h.cap = cap
     st = pm_stats()
-    o = options(strategy, slots, chunk, ranges_per_sm, accumulator)
+    o = options(strategy, slots, chunk, ranges_per_sm, accumulator, cost_row, cost_window)
     rc = lib().pm_polymul(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(o),
                           C.byref(st), _stream_handle(stream))
     if rc != PM_OK:
@@ -389,8 +392,26 @@ def _batch_lib():
         L.pm_batch_polymul.argtypes = [P(pm_batch_item), C.c_uint32, P(pm_batch_options), P(pm_batch_stats),
                                        C.c_void_p]
         L.pm_batch_polymul.restype = C.c_int
+        L.pm_batch_workspace.argtypes = [P(pm_batch_item), C.c_uint32, P(pm_batch_options), P(C.c_uint64),
+                                         P(C.c_uint64)]
+        L.pm_batch_workspace.restype = C.c_int
         _batch_ready = True
     return L
+
+
+def batch_workspace(products, range_target: int = 0, ranges_per_item: int = 0):
+    """(device bytes, host bytes) the batched pass needs for `products`
+    (pm_batch_workspace; host arithmetic only)."""
+    n = len(products)
+    items = (pm_batch_item * n)()
+    for k, pr in enumerate(products):
+        items[k] = _batch_item(pr)
+    opt = pm_batch_options(range_target, ranges_per_item)
+    d, h = C.c_uint64(0), C.c_uint64(0)
+    rc = _batch_lib().pm_batch_workspace(items, n, C.byref(opt), C.byref(d), C.byref(h))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_batch_workspace")
+    return int(d.value), int(h.value)
 
 
 class BatchPlan:
@@ -576,7 +597,8 @@ class pm_batch_tune_report(C.Structure):
 
 def _opts_dict(o: pm_options) -> dict:
     return dict(strategy=STRATEGY_NAME.get(o.strategy, o.strategy), slots=o.slots, chunk=o.chunk,
-                ranges_per_sm=o.ranges_per_sm, accumulator={v: k for k, v in ACCUMULATOR.items()}.get(o.accumulator))
+                ranges_per_sm=o.ranges_per_sm, accumulator={v: k for k, v in ACCUMULATOR.items()}.get(o.accumulator),
+                cost_row=o.cost_row, cost_window=o.cost_window)
 
 
 def autotune(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61", stream=None):

@@ -255,7 +255,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (f->n == 0 || g->n == 0) return finish(0);
     Layout raw = L;
     const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
-    if (!opt || (!o.strategy && !o.slots && !o.chunk && !o.ranges_per_sm && !o.accumulator)) {
+    if (!opt || (!o.strategy && !o.slots && !o.chunk && !o.ranges_per_sm && !o.accumulator && !o.cost_row &&
+                 !o.cost_window)) {
         // default options: use the autotuner's choice for this shape class
         const unsigned __int128 pr = (unsigned __int128)f->n * g->n;
         const u64 bound = pr < raw_box ? (u64)pr : raw_box;
@@ -354,7 +355,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         const u32 Gn = (u32)G64;
         u32 l = 1;
         while ((u64)(l + 1) * (l + 1) < 256ull * Gn && l < 4096) l++;
-        const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, 1.0);
+        const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, slots,
+                                      o.cost_row ? o.cost_row : 12u, o.cost_window ? o.cost_window : 23000u);
         okey = S.get<u64>(end - lo);
         ocoef = S.get<u64>((end - lo) * words);
         ucount = S.get<u64>(Gn + 1);

@@ -3,9 +3,10 @@
 // Work split: the output rank interval [lo, end) is cut into G groups with
 // about equal cost.  Cost is sampled by the almost regular grid of Sec. 5
 // (each grid point gamma_{i,j} stands for the same number of term products,
-// as the paper's first step intends) plus a per-rank cost for the slots a
-// CTA clears and scans; both go into a histogram over the interval, and the
-// group boundaries sit where its cumulative cost crosses m / G of the total.
+// as the paper's first step intends) plus each rank's share of the window
+// costs (rows of f staged per window, fixed work per window); both go into
+// a histogram over the interval, and the group boundaries sit where its
+// cumulative cost crosses m / G of the total.
 // One CTA owns one group, so no two CTAs ever write the same output term
 // (Alg. 1, second step).
 //
@@ -518,11 +519,56 @@ __global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__rest
     atomicAdd(&hist[k], wg);
 }
 
-// every bucket also carries the cost of the slots it spans
-__global__ void k_hist_add(u64 *__restrict__ hist, u64 nbk, u64 wu)
+// Every bucket also carries its share of the window costs.  A window of
+// `win` ranks starting at the bucket stages the rows of f whose products
+// can land in it -- alpha_i in [x - beta_max, x + win - beta_min) -- and the
+// accumulate kernel's time per group measures as about
+//     products + cost_row (rows staged over its windows) + cost_window (windows)
+// in units of one term product, with cost_row 5 to 20 and cost_window
+// about 23000 (per-group timings of the dense workloads; 12 and 23000 by
+// default, the autotuner picks the weights per shape class).  K_b = cost_row rows + cost_window is
+// a window's cost near bucket b; a bucket of bw ranks carries bw / win of
+// it (kw keeps K_b for the refinement below).
+__global__ void k_hist_rows(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, u64 lo, u64 bw,
+                            u64 win, u64 nbk, u64 cost_row, u64 cost_window, u64 *__restrict__ hist,
+                            u64 *__restrict__ kw)
 {
-    u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < nbk) hist[k] += wu;
+    const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbk) return;
+    const u64 bmin = B[0], bmax = B[nb - 1];
+    const u64 x0 = lo + k * bw, x1 = x0 + win;
+    const u32 i_lo = x0 > bmax ? lower_bound_u64(A, na, x0 - bmax) : 0u;
+    const u32 i_hi = x1 > bmin ? lower_bound_u64(A, na, x1 - bmin) : 0u;
+    const u64 rows = i_hi > i_lo ? i_hi - i_lo : 0;
+    const u64 K = cost_row * rows + cost_window;
+    kw[k] = K;
+    hist[k] += (u64)(((unsigned __int128)K * bw) / win) + 1;
+}
+
+// A group narrower than a window still pays one whole window, which the
+// per-bucket share above charged only span / win of: its buckets get the
+// rest, K_b bw (1 / span - 1 / win), before the groups are cut again.
+__global__ void k_hist_narrow(const u64 *__restrict__ gb, u32 G, u64 lo, u64 bw, u64 win, u64 nbk,
+                              const u64 *__restrict__ kw, u64 *__restrict__ hist)
+{
+    const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nbk) return;
+    const u64 x0 = lo + k * bw;
+    // the group holding x0: last g with gb[g] <= x0
+    u32 a = 0, n = G;
+    while (n > 1) {
+        const u32 h = n >> 1;
+        if (gb[a + h] <= x0) {
+            a += h;
+            n -= h;
+        } else {
+            n = h;
+        }
+    }
+    const u64 span = gb[a + 1] - gb[a];
+    if (span == 0 || span >= win) return;
+    const unsigned __int128 add = ((unsigned __int128)kw[k] * bw * (win - span)) / ((unsigned __int128)span * win);
+    hist[k] += (u64)add;
 }
 
 // group m starts at the first bucket whose cumulative cost reaches m W / G
@@ -548,11 +594,11 @@ __global__ void k_group_bounds(const u64 *__restrict__ cw, u64 nbk, u32 G, u64 l
 }
 
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l, u64 products, double slot_cost)
+                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window)
 {
     // cost model: a grid point of the pp-matrix stands for products / ng
-    // term products; a rank of the interval for slot_cost (clearing,
-    // scanning and edge finding of its slot)
+    // term products; a bucket also carries its share of the window costs
+    // (rows staged and per-window work, k_hist_rows)
     u32 l = grid_l ? grid_l : 1;
     u32 si = na / l ? na / l : 1, sj = nb / l ? nb / l : 1;
     u32 stagger = (u32)(nb / (2ull * l));
@@ -564,14 +610,22 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     u64 *hist = S.get<u64>(nbk), *cw = S.get<u64>(nbk + 1);
     PM_CUDA(cudaMemsetAsync(hist, 0, nbk * 8, c.s));
     const u64 wg = products / ng + 1;
-    const u64 wu = (u64)(slot_cost * (double)bw) + 1;
     k_grid_hist<<<(unsigned)((ng + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, ng, lo, bw, nbk,
                                                                wg, hist);
     PM_LAUNCHED(c);
-    k_hist_add<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(hist, nbk, wu);
+    u64 *kw = S.get<u64>(nbk);
+    const u64 w = win ? win : 1;
+    k_hist_rows<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, lo, bw, w, nbk, cost_row, cost_window,
+                                                                hist, kw);
     PM_LAUNCHED(c);
     scan_exclusive_u64(c, S, hist, cw, nbk);
     u64 *gb = S.get<u64>(G + 1);
+    k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cw, nbk, G, lo, end, bw, gb);
+    PM_LAUNCHED(c);
+    // one refinement: charge narrow groups their whole window, cut again
+    k_hist_narrow<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(gb, G, lo, bw, w, nbk, kw, hist);
+    PM_LAUNCHED(c);
+    scan_exclusive_u64(c, S, hist, cw, nbk);
     k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cw, nbk, G, lo, end, bw, gb);
     PM_LAUNCHED(c);
     return gb;

@@ -28,8 +28,11 @@ struct DirectArgs {
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
 u32 direct_max_slots(int kind, u64 min_n, int requested);
+// G + 1 group boundaries over [lo, end) with about equal cost; win: the
+// window width (slots) the accumulate kernel will use; a group costs
+// products + cost_row (rows staged) + cost_window (windows)
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l, u64 products, double slot_cost);
+                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window);
 // ev_k0 / ev_k1 (may be null): events recorded around the accumulate launch
 void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end,
                    cudaEvent_t ev_k0 = nullptr, cudaEvent_t ev_k1 = nullptr);

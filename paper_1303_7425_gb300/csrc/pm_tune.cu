@@ -4,8 +4,9 @@
 // with several values and keeping the fastest (Sec. 5, Sec. 7).  This
 // library has more knobs -- the per-range strategy (direct-addressed slots
 // or sort + reduce), the window size in slots (the tile), the number of
-// groups per SM (the partition count), the slot accumulator, and for
-// batches the term products per range and ranges per work item -- and tunes
+// groups per SM (the partition count), the slot accumulator, the weights
+// of the group cost model, and for batches the term products per range and
+// ranges per work item -- and tunes
 // them the same way: every candidate runs on the caller's inputs, is timed
 // with CUDA events on the caller's stream, and the fastest is kept for the
 // problem's shape class.  pm_polymul called with default options looks the
@@ -108,7 +109,7 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
     const u64 raw_box = bound;
 
     std::vector<pm_options> cand;
-    auto add = [&](int strategy, u32 slots, u32 gps, int acc, u32 chunk) {
+    auto add = [&](int strategy, u32 slots, u32 gps, int acc, u32 chunk, u32 crow = 0, u32 cwin = 0) {
         pm_options o;
         memset(&o, 0, sizeof(o));
         o.strategy = strategy;
@@ -116,12 +117,19 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
         o.ranges_per_sm = gps;
         o.accumulator = acc;
         o.chunk = chunk;
+        o.cost_row = crow;
+        o.cost_window = cwin;
         cand.push_back(o);
     };
-    // direct-addressed: partition count x tile x accumulator
+    // direct-addressed: partition count x tile x accumulator, and the
+    // group cost model's weights
     for (u32 gps : {1u, 2u, 4u})
         for (u32 slots : {0u, 8192u}) add(PM_STRATEGY_DIRECT, slots, gps, PM_ACC_AUTO, 0);
     add(PM_STRATEGY_DIRECT, 0, 1, PM_ACC_WIDE, 0);
+    for (u32 gps : {1u, 2u}) {
+        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 20, 50000);
+        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 3, 5000);
+    }
     // sort + reduce: chunk sizes
     for (u32 chunk : {2048u, 4096u}) add(PM_STRATEGY_SORT, 0, 0, PM_ACC_AUTO, chunk);
 

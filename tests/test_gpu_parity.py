@@ -26,6 +26,7 @@ STRATS = [
     dict(strategy="direct", accumulator="limbs", slots=2048),
     dict(strategy="direct", slots=512),            # many ranges, ragged tails
     dict(strategy="direct", slots=1000, ranges_per_sm=64),
+    dict(strategy="direct", ranges_per_sm=3, cost_row=1, cost_window=1),   # other group boundaries
     dict(strategy="sort"),
     dict(strategy="sort", chunk=256),              # single-monomial ranges above the chunk
     dict(strategy="sort", chunk=1000),

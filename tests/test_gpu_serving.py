@@ -65,19 +65,28 @@ def test_serving_results_equal_alone_and_oracle():
 
 
 def test_serving_budget_admission():
+    """All requests queued at once under an HBM budget a third of what the
+    whole stream needs as one batch: admission must split it into at least
+    three batches, every request must succeed, and a request that cannot
+    fit the budget alone must fail with PM_ENOMEM."""
+    import paper_1303_7425_gb300 as P
     from paper_1303_7425_gb300.serving import serve
-    ws, t = _stream(count=40, dense=0, seed=23, rate=1e6, hi=400)
+    ws, _ = _stream(count=40, dense=0, seed=23, rate=1e6, hi=400)
+    prods = [_prod(w) for w in ws]
+    whole = P.batch_workspace(prods)[0]
+    alone = max(P.batch_workspace([p])[0] for p in prods)
+    budget = max(alone, whole // 3)
+    assert whole > 2 * budget                          # one batch cannot hold half the stream
     huge = polygen.sparse_product(polygen.Stream(99, 0), 4, 4096, 4096)     # 16.7M products
     ws.append(huge)
-    t = np.append(t, t[-1])
-    prods = [_prod(w) for w in ws]
-    # 8 MiB of arena: every small product fits alone (<= 160,000 products),
-    # the stream as a whole does not, and the huge request never fits
-    rep = serve(list(zip(t.tolist(), prods)), [w.term_products for w in ws],
-                server_kwargs=dict(streams=2, max_batch=64, device_budget=8 << 20))
+    prods.append(_prod(huge))
+    assert P.batch_workspace([prods[-1]])[0] > budget
+    t = [0.0] * len(ws)
+    rep = serve(list(zip(t, prods)), [w.term_products for w in ws],
+                server_kwargs=dict(streams=2, max_batch=64, device_budget=budget))
     assert rep["done"][len(ws) - 1]["status"] == -5
     assert all(rep["done"][k]["status"] == 0 for k in range(len(ws) - 1))
-    assert rep["state"]["batches"] > 2                 # admission split the stream into several batches
+    assert rep["state"]["batches"] >= 3                # admission split the stream
     for k in range(0, len(ws) - 1, 7):
         w = ws[k]
         e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
