@@ -41,6 +41,15 @@ WORKLOAD = ("dense 4-variable product: f, g = all 10,626 monomials of total degr
 FLUSH_BYTES = 256 << 20
 
 
+def hbm_peak():
+    """(GB/s, source) -- the measured copy bandwidth of the GB300s."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,9 +390,20 @@ def bench_batched(P, torch, count, tune=True):
         ok = n == len(e) and np.array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)
         checked += 1 if ok else 0
     ms = statistics.mean(times)
+    # the pass's HBM roofline: every input term read once (exponents and
+    # coefficient), every result term written once (key and coefficient)
+    n_out = sum(n for _, n in res)
+    in_bytes = sum((w.f.n + w.g.n) * (4 * w.nvars + 8) for w in ws)
+    alg_bytes = in_bytes + 16 * n_out
+    peak, peak_src = hbm_peak()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
     del prods
     torch.cuda.empty_cache()
     return {"products": count, "term_products": tp, "batched_ms": ms, "batched_value": tp / (ms * 1e-3),
+            "result_terms": n_out,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "algorithmic_bytes": alg_bytes, "peak_source": peak_src,
+                         "scope": "the whole batched pass (B1-B4) per graph replay"},
             "plain_ms": plain_ms, "plain_value": tp / (plain_ms * 1e-3), "batched_vs_plain_speedup": plain_ms / ms,
             "unit": UNIT, "options": best, "ranges": st["n_ranges"], "work_items": st["work_items"],
             "graph": bool(st["graph"]), "failed": failed, "oracle_checked": checked,
