@@ -15,8 +15,9 @@
 //       shared memory so FindEdge for the next range is a short gallop, and
 //       sorts and reduces each range in shared memory (ranges with more
 //       products than fit are bisected by key);
-//   B4  one CTA per product concatenates its ranges in ascending order into
-//       the caller's output and reports the result size or an error.
+//   B4  one CTA per product sizes its result, checks the capacity and
+//       places its ranges in ascending order; then warps on all SMs copy
+//       the ranges into the callers' outputs.
 // No two CTAs write the same output term.  Scratch for range results is
 // claimed from a device bump counter, bounded by the products' term
 // products.
@@ -79,6 +80,7 @@ struct BArgs {
     u32 cw;
     u32 target;                   // term products per range
     u32 per_item;                 // ranges per work item
+    u64 rg_total;                 // range slots of the batch
 };
 
 // ---------------------------------------------------------------------------
@@ -694,20 +696,24 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
 
 // ---------------------------------------------------------------------------
 // B4: concatenate each product's ranges into its output
+//   B4a (one CTA per product): sizes, capacity check, and per range its
+//       place in the output -- written over the range's bounds, which B3
+//       no longer needs: rlo = destination offset, rhi = product index (or
+//       SKIP for a range slot that is not copied);
+//   B4b (all SMs): warps copy ranges, so one large product's copy is
+//       spread over the whole GPU.
 // ---------------------------------------------------------------------------
+
+constexpr u64 SKIP = ~0ull;
 
 __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
 {
     __shared__ u64 ws[32];
-    __shared__ u64 fo[FIN_T];
-    const u32 p = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const u32 p = blockIdx.x, tid = threadIdx.x;
     BDesc &d = a.D[p];
-    if (d.status) {
-        if (tid == 0) d.n_out = 0;
-        return;
-    }
-    const u32 nr = d.nranges;
-    const u64 *rb = a.rbase + d.rg_off, *rc = a.rcount + d.rg_off;
+    const u32 nr = d.status ? 0u : d.nranges;
+    u64 *rlo = a.rlo + d.rg_off, *rhi = a.rhi + d.rg_off;
+    const u64 *rc = a.rcount + d.rg_off;
     u64 total = 0;
     for (u32 k0 = 0; k0 < nr; k0 += FIN_T) {
         const u32 k = k0 + tid;
@@ -715,36 +721,44 @@ __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
         block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
         total += cnt;
     }
-    if (total > d.hcap) {
-        if (tid == 0) {
-            d.n_out = total;
-            d.status |= ST_CAPACITY;
-        }
-        return;
-    }
+    const bool fits = total <= d.hcap;
     u64 run = 0;
-    for (u32 k0 = 0; k0 < nr; k0 += FIN_T) {
+    for (u32 k0 = 0; k0 < d.rcap; k0 += FIN_T) {
         const u32 k = k0 + tid;
         u64 cnt;
-        fo[tid] = run + block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
-        __syncthreads();
-        // warp w copies ranges k0 + w, k0 + w + 16, ...
-        for (u32 q = w; q < FIN_T && k0 + q < nr; q += FIN_T / 32) {
-            const u64 src = rb[k0 + q], dst = fo[q], n = rc[k0 + q];
-            for (u64 t = lane; t < n; t += 32) {
-                d.hkey[dst + t] = a.skey[src + t];
-                if (d.kind == PM_COEF_M61) {
-                    d.hcoef[dst + t] = a.scoef[a.cw * (src + t)];
-                } else {
-                    d.hcoef[2 * (dst + t)] = a.scoef[2 * (src + t)];
-                    d.hcoef[2 * (dst + t) + 1] = a.scoef[2 * (src + t) + 1];
-                }
-            }
+        const u64 at = run + block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
+        if (k < d.rcap) {
+            const bool copy = fits && k < nr;
+            rlo[k] = copy ? at : 0;
+            rhi[k] = copy ? (u64)p : SKIP;
         }
         run += cnt;
-        __syncthreads();
     }
-    if (tid == 0) d.n_out = total;
+    if (tid == 0) {
+        d.n_out = d.status ? 0 : total;
+        if (!fits && !d.status) d.status |= ST_CAPACITY;
+    }
+}
+
+__global__ void __launch_bounds__(256) kb_copy(BArgs a)
+{
+    const u32 lane = threadIdx.x & 31;
+    const u64 warps = (u64)gridDim.x * (blockDim.x >> 5);
+    for (u64 r = ((u64)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < a.rg_total; r += warps) {
+        const u64 p = a.rhi[r];
+        if (p == SKIP) continue;
+        const BDesc &d = a.D[p];
+        const u64 src = a.rbase[r], dst = a.rlo[r], n = a.rcount[r];
+        for (u64 t = lane; t < n; t += 32) {
+            d.hkey[dst + t] = a.skey[src + t];
+            if (d.kind == PM_COEF_M61) {
+                d.hcoef[dst + t] = a.scoef[a.cw * (src + t)];
+            } else {
+                d.hcoef[2 * (dst + t)] = a.scoef[2 * (src + t)];
+                d.hcoef[2 * (dst + t) + 1] = a.scoef[2 * (src + t) + 1];
+            }
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -890,6 +904,7 @@ static BArgs carve_ws(unsigned char *base, u32 count, const BatchSizes &z)
     a.cw = z.cw;
     a.target = z.target;
     a.per_item = z.per_item;
+    a.rg_total = z.rg_total;
     return a;
 }
 
@@ -912,6 +927,8 @@ static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
     kb_ranges<<<sm_count, RNG_T, RNG_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
     kb_finish<<<a.count, FIN_T, 0, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_copy<<<sm_count * 8, 256, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());
 }
 

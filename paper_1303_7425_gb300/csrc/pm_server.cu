@@ -203,17 +203,11 @@ void fail_now(pm_server *s, const Req &r, int code)
     s->done.push_back(d);
 }
 
-// admit and launch as many batches as stream slots and memory allow
+// admit and launch as many batches as stream slots and memory allow (the
+// pending queue holds only products the batch kernels take)
 void launch(pm_server *s)
 {
     for (;;) {
-        // products too large for the batch kernels go to the worker
-        while (!s->pending.empty() && !fits_batch(s->pending.front().item)) {
-            std::lock_guard<std::mutex> lk(s->mu);
-            s->big.push_back(s->pending.front());
-            s->pending.pop_front();
-            s->cv.notify_one();
-        }
         if (s->pending.empty()) return;
         int slot = -1;
         for (size_t k = 0; k < s->streams.size(); k++)
@@ -222,11 +216,11 @@ void launch(pm_server *s)
                 break;
             }
         if (slot < 0) return;
-        // the longest prefix of batchable requests whose workspace fits
+        // the longest prefix of the queue whose workspace fits
         std::vector<pm_batch_item> items;
         size_t take = 0;
         u64 dbytes = 0, hbytes = 0;
-        while (take < s->pending.size() && take < s->cfg.max_batch && fits_batch(s->pending[take].item)) {
+        while (take < s->pending.size() && take < s->cfg.max_batch) {
             items.push_back(s->pending[take].item);
             u64 db = 0, hb = 0;
             try {
@@ -353,7 +347,15 @@ extern "C" int pm_server_submit(pm_server *s, const pm_batch_item *item, uint64_
     r.tag = tag;
     r.t_submit = s->now();
     r.t_admit = 0;
-    s->pending.push_back(r);
+    if (fits_batch(r.item)) {
+        s->pending.push_back(r);
+    } else {
+        // too large for the batch kernels: straight to the worker, so it
+        // neither waits behind nor splits the batches of small requests
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->big.push_back(r);
+        s->cv.notify_one();
+    }
     return PM_OK;
 }
 
