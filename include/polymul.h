@@ -262,7 +262,7 @@ typedef struct pm_batch_item {
 
 typedef struct pm_batch_options {
     uint32_t range_target;     /* term products per output range (64..3072;
-                                  default 1536)                                   */
+                                  default 2048)                                   */
     uint32_t ranges_per_item;  /* consecutive ranges per work item (default 16)   */
 } pm_batch_options;
 

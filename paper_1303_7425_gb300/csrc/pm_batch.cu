@@ -40,6 +40,9 @@ constexpr int RNG_IPT = RNG_CHUNK / RNG_T;
 constexpr u32 RNG_W = RNG_T / 32;
 constexpr u32 RNG_LANE_MAX = (RNG_CHUNK / RNG_W + 31) / 32;  // products (or pairs) per lane of a piece
 constexpr u32 ROWS_PER_T = BT_MAX_TERMS / RNG_T;  // 16
+constexpr u32 RNG_BS = BT_MAX_TERMS;               // g keys staged in shared memory (larger g: read via L1)
+constexpr int RNG_CTAS = 1;                        // B3 CTAs per SM
+constexpr u32 RNG_TARGET_DEFAULT = 2 * RNG_CHUNK / 3;  // term products per range unless tuned
 constexpr int FIN_T = 512;
 
 // per-product descriptor (device); fields after `out_` are written by the
@@ -348,15 +351,15 @@ struct RngSmem {
 };
 
 // sort histogram; also holds a piece's compacted row tables
-constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256;
-constexpr size_t RNG_SMEM = (size_t)BT_MAX_TERMS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
+constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
+constexpr size_t RNG_SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
                             RNG_HIST_WORDS * 4;
 
 __device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
 {
     RngSmem m;
     m.Bs = (u64 *)p;
-    m.kA = m.Bs + BT_MAX_TERMS;
+    m.kA = m.Bs + RNG_BS;
     m.kB = m.kA + RNG_CHUNK;
     m.cv = m.kB + RNG_CHUNK;
     m.hist = (u32 *)(m.cv + 2 * RNG_CHUNK);
@@ -569,7 +572,7 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
     return wrote;
 }
 
-__global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
+__global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
@@ -595,7 +598,13 @@ __global__ void __launch_bounds__(RNG_T, 1) kb_ranges(BArgs a)
         const u64 *Gk = Fk + d.nf, *Gc = Fc + d.nf;
         const u64 *A = swap ? Gk : Fk, *Ac = swap ? Gc : Fc;
         const u64 *Bg = swap ? Fk : Gk, *Bc = swap ? Fc : Gc;
-        for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
+        // g's keys in shared memory when they fit, else read through L1
+        m.Bs = (u64 *)smem;
+        if (cg <= RNG_BS) {
+            for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
+        } else {
+            m.Bs = const_cast<u64 *>(Bg);
+        }
         __syncthreads();
         // rows of this thread: [r0, r1), ceil(cf / RNG_T) <= ROWS_PER_T of
         // them, so every thread has work; cursors at the first range's start
@@ -825,7 +834,7 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     BatchSizes z;
-    z.target = o.range_target ? o.range_target : 1536;
+    z.target = o.range_target ? o.range_target : RNG_TARGET_DEFAULT;
     z.per_item = o.ranges_per_item ? o.ranges_per_item : 16;
     if (z.target < 64 || z.target > RNG_CHUNK || z.per_item < 1 || z.per_item > 4096)
         throw Error(PM_EINVAL, "bad batch options");
@@ -924,7 +933,7 @@ static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
     PM_CUDA(cudaGetLastError());
     kb_plan<<<a.count, PLAN_T, PLAN_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
-    kb_ranges<<<sm_count, RNG_T, RNG_SMEM, s>>>(a);
+    kb_ranges<<<sm_count * RNG_CTAS, RNG_T, RNG_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
     kb_finish<<<a.count, FIN_T, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());
@@ -1088,6 +1097,8 @@ int batch_collect_ws(pm_batch_item *items, u32 count, const void *hws)
 }
 
 void batch_prepare_device() { set_batch_smem(); }
+
+u32 batch_range_chunk() { return RNG_CHUNK; }
 
 }  // namespace pm
 

@@ -50,6 +50,8 @@ ShapeKey shape_key(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box)
 }
 
 // used by pm_polymul when its options are all defaults
+u32 batch_range_chunk();  // pm_batch.cu
+
 bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box, pm_options &o)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -173,7 +175,9 @@ extern "C" int pm_batch_autotune(const pm_batch_item *items, uint32_t count, pm_
     float best_ms = 1e30f;
     int best_k = -1;
     int k = 0;
-    for (uint32_t target : {1024u, 1536u, 2048u, 3072u}) {
+    // range sizes: fractions of the range kernel's shared-memory chunk
+    const u32 ch = batch_range_chunk();
+    for (uint32_t target : {ch / 3, ch / 2, 2 * ch / 3, ch}) {
         for (uint32_t per : {8u, 16u, 64u}) {
             pm_batch_options o = {target, per};
             pm_batch_plan *pl = nullptr;
