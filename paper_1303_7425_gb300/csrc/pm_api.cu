@@ -355,11 +355,11 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         const u32 Gn = (u32)G64;
         u32 l = 1;
         while ((u64)(l + 1) * (l + 1) < 256ull * Gn && l < 4096) l++;
+        const u32 crow = o.cost_row ? o.cost_row : 12u, cwin = o.cost_window ? o.cost_window : 23000u;
         const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, slots,
-                                      o.cost_row ? o.cost_row : 12u, o.cost_window ? o.cost_window : 23000u);
+                                      crow, cwin);
         okey = S.get<u64>(end - lo);
         ocoef = S.get<u64>((end - lo) * words);
-        ucount = S.get<u64>(Gn + 1);
         DirectArgs a;
         memset(&a, 0, sizeof(a));
         a.A = F.rank;
@@ -375,16 +375,17 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         a.lo = lo;
         a.okey = okey;
         a.ocoef = ocoef;
-        a.ucount = ucount;
         a.L = L;
         a.abort = abort;
         if (st) PM_CUDA(cudaEventRecord(e0, c.s));
-        launch_direct(c, S, a, slots, kind, o.accumulator, end, k0, k1);
+        launch_direct(c, S, a, slots, kind, o.accumulator, end, crow, cwin, k0, k1);
         if (st) PM_CUDA(cudaEventRecord(e1, c.s));
         stats.n_ranges = Gn;
-        slice_base = const_cast<u64 *>(gb);
+        // the result slices are the windows, in rank order
+        ucount = a.ucount;
+        slice_base = const_cast<u64 *>(a.W);
         slice_base0 = lo;
-        nslices = Gn;
+        nslices = (u32)a.nwin_max;
     } else {
         // K-b: grid splitters, counts, refinement to the chunk capacity
         PartitionPlan plan;

@@ -353,22 +353,26 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
     acc.carve(smem);
     DTables t = carve_dtables(smem + (size_t)Acc<ACC>::slots * Acc<ACC>::bytes);
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const u32 g = blockIdx.x;
-    if (g >= a.ngroups) return;
+    __shared__ u32 s_next;
     // inputs that no longer match a replayed plan could put products
-    // outside the windows; such a replay computes nothing
-    if (a.abort && *a.abort) {
-        if (tid == 0) a.ucount[g] = 0;
-        return;
-    }
-    const u64 obase = a.gb[g] - a.lo;
+    // outside the windows; such a replay computes nothing (the window
+    // counts stay zero)
+    if (a.abort && *a.abort) return;
     const u32 nb = a.nb, na = a.na;
-    u64 run = 0;
+    const u64 nwin = a.wpos[a.ngroups];
     // every slot starts at zero; each window's emission clears the slots
     // it read, so the next window starts from zero again
     for (u32 x = tid; x < Acc<ACC>::slots; x += DT) acc.zero(x);
 
-    for (u64 bw = a.wpos[g], bend = a.wpos[g + 1]; bw < bend; bw++) {
+    // persistent: take windows from a device counter, most expensive first
+    // (the order k_window_order wrote), so the cheap ones fill the tail
+    for (;;) {
+        if (tid == 0) s_next = atomicAdd(a.wnext, 1u);
+        __syncthreads();
+        const u32 wk = s_next;
+        __syncthreads();
+        if (wk >= nwin) break;
+        const u64 bw = a.order[wk];
         const u64 lo = a.W[bw], hi = a.W[bw + 1];
         const u32 span = (u32)(hi - lo);
         if (a.cnt[bw + 1] == a.cnt[bw]) continue;  // no term product lands in this window
@@ -466,7 +470,9 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         }
         u64 wtot;
         const u64 wbase = block_exclusive_scan(lane == 0 ? wcount : 0, wtot, ws);
-        u64 put = obase + run + __shfl_sync(0xffffffffu, wbase, 0);
+        // the window's terms go to its own part of the scratch, at its
+        // first rank; compaction concatenates the windows in rank order
+        u64 put = (lo - a.lo) + __shfl_sync(0xffffffffu, wbase, 0);
         for (u32 sb = s0; sb < s1; sb += 32) {
             const u32 s = sb + lane;
             u64 v0 = 0, v1 = 0;
@@ -485,10 +491,42 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             }
             put += __popc(bal);
         }
-        run += wtot;
+        if (tid == 0) a.ucount[bw] = wtot;
         __syncthreads();
     }
-    if (tid == 0) a.ucount[g] = run;
+}
+
+// Order of the windows for the persistent accumulate kernel: descending
+// estimated cost (term products + cost_row rows staged + cost_window), by
+// 64 power-of-two classes -- largest-first scheduling needs no more than an
+// approximate order.  One CTA; windows at and past the device's window count
+// are not listed.
+__global__ void __launch_bounds__(1024) k_window_order(const u64 *__restrict__ cnt, const u32 *__restrict__ i0s,
+                                                       const u32 *__restrict__ i1s, const u64 *__restrict__ nwin_p,
+                                                       u64 cost_row, u64 cost_window, u32 *__restrict__ order)
+{
+    __shared__ u32 hist[64];
+    __shared__ u32 base[64];
+    const u64 nwin = *nwin_p;
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    auto cls = [&](u64 b) {
+        const u64 prod = cnt[b + 1] - cnt[b];
+        const u64 rows = i1s[b + 1] > i0s[b] ? i1s[b + 1] - i0s[b] : 0;
+        const u64 cost = prod ? prod + cost_row * rows + cost_window : 0;
+        return cost ? 63u - (u32)(63 - __clzll((long long)cost)) : 63u;  // 0 = most expensive
+    };
+    for (u64 b = threadIdx.x; b < nwin; b += blockDim.x) atomicAdd(&hist[cls(b)], 1u);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u32 run = 0;
+        for (int k = 0; k < 64; k++) {
+            base[k] = run;
+            run += hist[k];
+        }
+    }
+    __syncthreads();
+    for (u64 b = threadIdx.x; b < nwin; b += blockDim.x) order[atomicAdd(&base[cls(b)], 1u)] = (u32)b;
 }
 
 // Weighted histogram of the cost samples over NBK buckets of [lo, end):
@@ -664,8 +702,8 @@ static void set_smem(K kernel, size_t bytes)
 }
 
 
-void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end,
-                   cudaEvent_t ev_k0, cudaEvent_t ev_k1)
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end, u32 cost_row,
+                   u32 cost_window, cudaEvent_t ev_k0, cudaEvent_t ev_k1)
 {
     const u32 G = a.ngroups;
     // window boundaries W (at most G + span / slots + 1 of them)
@@ -703,19 +741,30 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     }
     PM_LAUNCHED(c);
 
-    // accumulate, one CTA per group
+    // windows in descending cost, per-window result counts, the counter
+    a.order = S.get<u32>(nbmax);
+    a.ucount = S.get<u64>(nbmax + 1);
+    a.wnext = S.get<u32>(1);
+    a.nwin_max = nbmax;
+    PM_CUDA(cudaMemsetAsync(a.ucount, 0, (nbmax + 1) * 8, c.s));
+    PM_CUDA(cudaMemsetAsync(a.wnext, 0, 4, c.s));
+    k_window_order<<<1, 1024, 0, c.s>>>(a.cnt, a.i0s, a.i1s, wpos + G, cost_row, cost_window, a.order);
+    PM_LAUNCHED(c);
+
+    // accumulate: persistent CTAs, one per SM
     const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
     const size_t bytes = (size_t)acc_stride(acc_bytes(acc)) * acc_bytes(acc) + DTABLE_BYTES;
+    const unsigned grid = (unsigned)(nbmax < (u64)c.sm_count ? nbmax : (u64)c.sm_count);
     if (ev_k0) PM_CUDA(cudaEventRecord(ev_k0, c.s));
     if (acc == ACC_W64) {
         set_smem(k_direct<ACC_W64>, bytes);
-        k_direct<ACC_W64><<<G, DT, bytes, c.s>>>(a, slots);
+        k_direct<ACC_W64><<<grid, DT, bytes, c.s>>>(a, slots);
     } else if (acc == ACC_L16) {
         set_smem(k_direct<ACC_L16>, bytes);
-        k_direct<ACC_L16><<<G, DT, bytes, c.s>>>(a, slots);
+        k_direct<ACC_L16><<<grid, DT, bytes, c.s>>>(a, slots);
     } else {
         set_smem(k_direct<ACC_I128>, bytes);
-        k_direct<ACC_I128><<<G, DT, bytes, c.s>>>(a, slots);
+        k_direct<ACC_I128><<<grid, DT, bytes, c.s>>>(a, slots);
     }
     PM_LAUNCHED(c);
     if (ev_k1) PM_CUDA(cudaEventRecord(ev_k1, c.s));

@@ -21,9 +21,12 @@ struct DirectArgs {
     u32 *i0s, *i1s;      // per boundary: first row reaching it, first row past it
     u64 *cnt;            // per boundary: term products with rank below it
     u64 *okey, *ocoef;   // output scratch
-    u64 *ucount;         // terms written per group
+    u64 *ucount;         // terms written per window (set by launch_direct, nwin_max + 1 entries)
     Layout L;
     const u32 *abort;    // non-zero: a replayed plan's inputs no longer match it (may be null)
+    u32 *order;          // windows, most expensive first (set by launch_direct)
+    u32 *wnext;          // window counter of the persistent accumulate kernel
+    u64 nwin_max;        // bound on the window count (host), slices for compaction
 };
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
@@ -33,8 +36,11 @@ u32 direct_max_slots(int kind, u64 min_n, int requested);
 // products + cost_row (rows staged) + cost_window (windows)
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
                    u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window);
+// Windows, FindEdge and the accumulate kernel.  On return a.W (window
+// starts), a.ucount (terms per window) and a.nwin_max describe the result
+// slices: window k's terms sit at a.W[k] - a.lo in the output scratch.
 // ev_k0 / ev_k1 (may be null): events recorded around the accumulate launch
-void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end,
-                   cudaEvent_t ev_k0 = nullptr, cudaEvent_t ev_k1 = nullptr);
+void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int requested, u64 end, u32 cost_row,
+                   u32 cost_window, cudaEvent_t ev_k0 = nullptr, cudaEvent_t ev_k1 = nullptr);
 
 }  // namespace pm
