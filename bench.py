@@ -567,6 +567,15 @@ def run_ours(args):
                 "ms_per_step": statistics.mean(ms_3), "n_out": r3.n,
                 "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_3),
                 "kernel_frac_of_probe": w3.term_products / (statistics.mean(s["ms_range_kernel"] for s in st_3) * 1e-3) / peak}
+            # the paper's Example 1 at full size (Sec. 6): 1.84e10 term products
+            we = polygen.paper_example1()
+            pe = time_plan(P, torch, we, 5, 2, flush)
+            if pe:
+                extras["paper_example1"] = {
+                    "value": we.term_products / (statistics.mean(pe[0]) * 1e-3), "unit": UNIT,
+                    "ms_per_step": statistics.mean(pe[0]), "n_out": pe[1], "term_products": we.term_products,
+                    "workload": "f1 = (1+x+y+z+t)^40 times f1 + 1, mod 2^61-1 (plan replay)",
+                    "paper_context": "Fermi GPU, FP64 coefficients: 32 s; 64 Xeon cores, integers: 16.1 s (Sec. 6)"}
             c4 = bench_batched(P, torch, args.c4_count, tune=not args.no_tune)
             extras["c4_batched"] = c4
             # serving at ~70% of the measured capacity for the request mix:

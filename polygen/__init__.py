@@ -197,6 +197,19 @@ def workload_c2(kind: str = "m61", seed: Optional[int] = None) -> Workload:
                     "4 vars, all 10626 monomials of degree <= 20 on both sides")
 
 
+def paper_example1() -> Workload:
+    """Sec. 6, Example 1: f1 = (1 + x + y + z + t)^40 and g1 = f1 + 1, 135,751
+    terms each, coefficients mod 2^61 - 1 (the multinomial expansion; no
+    random draws)."""
+    e, c = multinomial_power(4, 40)
+    fc = np.array(c, dtype=np.uint64)
+    gc = fc.copy()
+    const = int(np.flatnonzero((e == 0).all(axis=1))[0])
+    gc[const] = (int(gc[const]) + 1) % P61
+    return Workload("paper_ex1_4v_pow40", 4, [16] * 4, "m61", Poly(e, fc), Poly(e.copy(), gc),
+                    "f1 = (1+x+y+z+t)^40, g1 = f1 + 1 (135,751 terms each)")
+
+
 C3_CAPS = (6, 8, 10, 12, 16)
 
 

@@ -377,3 +377,17 @@ def test_coef_at_matches_full_product():
     assert np.array_equal(got, hc[::7])
     absent = np.array([[13, 13, 13]], dtype=np.uint32)     # beyond the product's degree
     assert oracle.coef_at(3, [10] * 3, "m61", fe, fc, ge, gc, absent)[0] == 0
+
+
+def test_paper_example1_operands():
+    """Sec. 6, Example 1: f1 = (1+x+y+z+t)^40 has C(44, 4) = 135,751 terms,
+    the count the paper prints; g1 = f1 + 1 differs only in the constant."""
+    import math
+    w = polygen.paper_example1()
+    assert w.f.n == w.g.n == math.comb(44, 4) == 135751
+    diff = np.flatnonzero(w.f.coefs != w.g.coefs)
+    assert len(diff) == 1 and int(w.f.exps[diff[0]].sum()) == 0
+    assert int(w.g.coefs[diff[0]]) == 2                 # 1 from the expansion, 1 added
+    # x^40 has coefficient 1, x y z t^37 has 40!/37! = 59280
+    row = {tuple(e): int(c) for e, c in zip(w.f.exps.tolist(), w.f.coefs.tolist())}
+    assert row[(40, 0, 0, 0)] == 1 and row[(1, 1, 1, 37)] == 40 * 39 * 38
