@@ -92,6 +92,9 @@ typedef struct pm_terms_out {
 #define PM_STRATEGY_AUTO   0  /* autotuner's choice (default)                      */
 #define PM_STRATEGY_DIRECT 1  /* direct-addressed shared-memory accumulation       */
 #define PM_STRATEGY_SORT   2  /* shared-memory radix sort + segmented reduce       */
+#define PM_STRATEGY_HASH   3  /* hashed windows: a shared-memory hash table per
+                                 window of up to 2^32 ranks (sparse results in
+                                 large boxes)                                      */
 
 /* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
 /* Direct strategy accumulators (mod p kind). */
@@ -120,8 +123,9 @@ typedef struct pm_stats {
     uint64_t n_out;            /* result terms                                    */
     uint64_t n_ranges;         /* output key ranges (one CTA each)                */
     uint64_t box;              /* output-exponent box size used for ranks          */
-    int32_t strategy;          /* PM_STRATEGY_DIRECT or PM_STRATEGY_SORT          */
-    uint32_t refine_rounds;    /* partition refinement rounds                      */
+    int32_t strategy;          /* PM_STRATEGY_DIRECT, _SORT or _HASH              */
+    uint32_t refine_rounds;    /* partition refinement rounds (sort); window
+                                  rounds (hash)                                   */
     uint32_t kernel_launches;  /* kernels launched by the call                     */
     uint32_t host_syncs;       /* stream synchronisations by the call              */
     float ms_range_kernel;     /* device time of the accumulate kernel alone: one

@@ -222,7 +222,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 2 || o.accumulator < 0 || o.accumulator > 2)
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 2)
         throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
     memset(&stats, 0, sizeof(stats));
@@ -312,10 +312,19 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     u32 slots = o.slots ? o.slots : slots_max;
     if (slots > slots_max) throw Error(PM_EINVAL, "slots exceed shared memory");
     const u32 chunk = o.chunk ? o.chunk : DEFAULT_CHUNK;
+    // direct addressing's FindEdge table has a row of n_f words per window
+    const u64 edge_words = ((box + slots - 1) / slots + (u64)c.sm_count * 4 + 1) * F.n;
     if (strategy == PM_STRATEGY_AUTO) {
         // direct addressing pays when the rank box is not much larger than
-        // the work: every slot of the box is cleared and scanned once
-        strategy = box <= 16 * products && box < (1ull << 40) ? PM_STRATEGY_DIRECT : PM_STRATEGY_SORT;
+        // the work (every slot of the box is cleared and scanned once) and
+        // its windows' edge table stays within 2^30 words; a box up to 64
+        // times the work takes hashed windows; sparser products the sort
+        if (box <= 16 * products && box < (1ull << 40) && edge_words <= (1ull << 30))
+            strategy = PM_STRATEGY_DIRECT;
+        else if (box <= 64 * products)
+            strategy = PM_STRATEGY_HASH;
+        else
+            strategy = PM_STRATEGY_SORT;
     }
     if (strategy == PM_STRATEGY_DIRECT && box >= (1ull << 40))
         throw Error(PM_EINVAL, "exponent box too large for the direct strategy");
@@ -323,6 +332,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (rec) rec->direct = strategy == PM_STRATEGY_DIRECT;
     // the sort strategy's partition refinement reads counts on the host
     if (capture && strategy != PM_STRATEGY_DIRECT) throw Error(PM_ECUDA, "plan: only the direct path is captured");
+
 
     u64 *okey, *ocoef, *ucount, *foff, *slice_base;
     u64 slice_base0;
@@ -340,6 +350,51 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (st)
         for (cudaEvent_t &x : ev.e) PM_CUDA(cudaEventCreate(&x));
     cudaEvent_t e0 = ev.e[0], e1 = ev.e[1], k0 = ev.e[2], k1 = ev.e[3];
+
+    if (strategy == PM_STRATEGY_HASH) {
+        // hashed windows: rounds with host reads, then the result written
+        // straight to h
+        u32 *g32 = S.get<u32>(G.n);
+        operand_ranks(c, F, L, nullptr);
+        operand_ranks(c, G, L, g32);
+        const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
+        const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        HashInputs in;
+        in.A = F.rank;
+        in.Ac = F.coef;
+        in.B = G.rank;
+        in.Bc = G.coef;
+        in.B32 = g32;
+        in.na = (u32)F.n;
+        in.nb = (u32)G.n;
+        in.L = L;
+        u32 rounds = 0;
+        if (st) PM_CUDA(cudaEventRecord(e0, c.s));
+        if (st) PM_CUDA(cudaEventRecord(k0, c.s));
+        const u64 n_out = hash_product(c, S, in, kind, o.accumulator, lo, end, products, (u64 *)h->keys,
+                                       (u64 *)h->coefs, h->cap, &rounds);
+        if (st) PM_CUDA(cudaEventRecord(k1, c.s));
+        if (st) PM_CUDA(cudaEventRecord(e1, c.s));
+        stats.refine_rounds = rounds;
+        PM_CUDA(cudaMemcpyAsync(&hs.status, &ds->status, sizeof(u32), cudaMemcpyDeviceToHost, c.s));
+        c.sync();
+        if (st) {
+            PM_CUDA(cudaEventElapsedTime(&stats.ms_range_step, e0, e1));
+            PM_CUDA(cudaEventElapsedTime(&stats.ms_range_kernel, k0, k1));
+        }
+        if (hs.status & ST_INTERNAL) throw Error(PM_ECUDA, "internal consistency check failed");
+        if (n_out > h->cap) {
+            h->n = n_out;
+            stats.n_out = n_out;
+            if (st) {
+                stats.kernel_launches = c.launches;
+                stats.host_syncs = c.syncs;
+                *st = stats;
+            }
+            return PM_ECAPACITY;
+        }
+        return finish(n_out);
+    }
 
     if (strategy == PM_STRATEGY_DIRECT) {
         // K-b: ranks, grid sample, groups (no host sync)

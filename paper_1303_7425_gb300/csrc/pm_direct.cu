@@ -16,6 +16,10 @@
 // first with gamma_{i,j} >= hi (FindEdge, Sec. 2); a separate kernel
 // computes them for every window boundary beforehand (k_find_edge), so the
 // accumulate kernel only reads them.
+#include <algorithm>
+#include <vector>
+
+#include "pm_blocksort.cuh"
 #include "pm_direct.cuh"
 
 namespace pm {
@@ -234,10 +238,11 @@ __device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t)
 // ---------------------------------------------------------------------------
 enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2 };
 
-template <int ACC>
+template <int ACC, u32 STRIDE = 0>
 struct Acc {
     static constexpr u32 bytes = ACC == ACC_W64 ? 12 : 16;
-    static constexpr u32 slots = acc_stride(bytes);  // array stride (the window may use fewer)
+    // array stride (a window may use fewer slots)
+    static constexpr u32 slots = STRIDE ? STRIDE : acc_stride(bytes);
     u64 *w;      // ACC_W64: sums; ACC_I128: lo words [0, slots), hi words [slots, 2 slots)
     u32 *c;      // ACC_W64: wrap counts; ACC_L16: limb counters, limb k at [k * slots, (k+1) * slots)
 
@@ -768,6 +773,371 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     }
     PM_LAUNCHED(c);
     if (ev_k1) PM_CUDA(cudaEventRecord(ev_k1, c.s));
+}
+
+// ---------------------------------------------------------------------------
+// Hashed windows: products whose result is sparse in a large rank box.
+//
+// A direct-addressed window holds one slot per rank, so a sparse box needs
+// so many windows that the FindEdge table (a row per window) and the row
+// staging per window explode.  Here a window may span up to 2^32 ranks; its
+// distinct result monomials go to a shared-memory hash table (HT slots,
+// linear probing, bounded), and FindEdge is done inside the kernel: for the
+// window's two boundaries each thread walks a staircase over a contiguous
+// chunk of rows (the row edges fall as the row rises, Sec. 2) and leaves the
+// column range of every row in a per-CTA scratch.  Emission sorts the
+// occupied slots by rank (block_sort_interval) and writes the window's
+// terms in order.  A window with more than HT_LOAD distinct monomials (or a
+// probe run longer than HT_PROBES) is abandoned and reported; the host
+// splits it in two and runs the halves in the next round.
+// ---------------------------------------------------------------------------
+
+constexpr u32 HT = 4096, HT_BITS = 12;
+constexpr u32 HT_LOAD = 3072;
+constexpr u32 HT_PROBES = 64;
+constexpr u32 HEMPTY = 0xFFFFFFFFu;
+constexpr u64 HFAILED = ~0ull;
+
+struct HashArgs {
+    const u64 *A, *Ac, *B, *Bc;  // canonical f and g: ranks (sorted) and coefficients
+    const u32 *B32;              // low 32 bits of g's ranks
+    u32 na, nb;
+    const u64 *wlo, *whi;        // the round's windows (rank bounds)
+    u32 nwin;
+    u32 *E2;                     // per CTA: column ranges of the window's rows, 2 * na words
+    u64 *okey, *ocoef;           // window w's terms at w * HT (coefficient words: words)
+    u64 *ucount;                 // terms of window w, or HFAILED
+    u32 *wnext;                  // window counter
+    Layout L;
+    u32 words;
+    const u32 *abort;
+};
+
+template <int ACC>
+__global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ u64 ws[32];
+    __shared__ u32 s_next, s_count, s_over, s_rows[2];
+    using HA = Acc<ACC, HT>;
+    u32 *keys = (u32 *)smem;
+    HA acc;
+    acc.carve(smem + HT * 4);
+    DTables t = carve_dtables(smem + HT * 4 + (size_t)HT * HA::bytes);
+    unsigned char *sb_ = smem + HT * 4 + (size_t)HT * HA::bytes + DTABLE_BYTES;
+    u64 *kA = (u64 *)sb_, *kB = kA + HT;
+    uint16_t *iA = (uint16_t *)(kB + HT), *iB = iA + HT;
+    u32 *hist = (u32 *)(iB + HT);  // HT_HIST words
+    const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (a.abort && *a.abort) return;
+    u32 *E2 = a.E2 + (size_t)blockIdx.x * 2 * a.na;
+    const u64 bmin = a.B[0], bmax = a.B[a.nb - 1];
+    for (u32 x = tid; x < HT; x += DT) {
+        keys[x] = HEMPTY;
+        acc.zero(x);
+    }
+    for (;;) {
+        if (tid == 0) {
+            s_next = atomicAdd(a.wnext, 1u);
+            s_count = 0;
+            s_over = 0;
+        }
+        __syncthreads();
+        const u32 wk = s_next;
+        if (wk >= a.nwin) break;
+        const u64 lo = a.wlo[wk], hi = a.whi[wk];
+        const u32 span = (u32)(hi - lo);
+        if (tid == 0) {
+            s_rows[0] = lo > bmax ? lower_bound_k(a.A, a.na, lo - bmax) : 0u;
+            s_rows[1] = hi > bmin ? lower_bound_k(a.A, a.na, hi - bmin) : 0u;
+        }
+        __syncthreads();
+        const u32 i0 = s_rows[0], i1 = s_rows[1];
+        // FindEdge for both boundaries: a staircase per thread chunk
+        {
+            const u32 per = (i1 - i0 + DT - 1) / DT;
+            const u32 r0 = i0 + tid * per, r1 = min(r0 + per, i1);
+            if (r0 < r1) {
+                u64 ar = a.A[r0];
+                u32 jl = lower_bound_k(a.B, a.nb, lo > ar ? lo - ar : 0);
+                u32 jh = lower_bound_k(a.B, a.nb, hi > ar ? hi - ar : 0);
+                E2[2 * (r0 - i0)] = jl;
+                E2[2 * (r0 - i0) + 1] = jh;
+                for (u32 r = r0 + 1; r < r1; r++) {
+                    ar = a.A[r];
+                    jl = walk_down(a.B, jl, lo > ar ? lo - ar : 0);
+                    jh = walk_down(a.B, jh, hi > ar ? hi - ar : 0);
+                    E2[2 * (r - i0)] = jl;
+                    E2[2 * (r - i0) + 1] = jh;
+                }
+            }
+        }
+        __syncthreads();
+        for (u32 base = i0; base < i1 && !s_over; base += DROWS) {
+            const u32 i = base + tid;
+            u32 jl = 0, len = 0, ra = 0;
+            u64 ca = 0;
+            if (i < i1) {
+                jl = E2[2 * (i - i0)];
+                len = E2[2 * (i - i0) + 1] - jl;
+                ra = (u32)a.A[i] - (u32)lo;
+                ca = a.Ac[i];
+            }
+            u64 total;
+            const u64 ex = block_exclusive_scan(len, total, ws);
+            t.off[tid] = (u32)ex;
+            t.rec[tid] = make_uint4((u32)ca, (u32)(ca >> 32), ra, jl - (u32)ex);
+            if (tid == 0) t.off[DROWS] = (u32)total;
+            const u32 nrows = min(i1 - base, (u32)DROWS);
+            __syncthreads();
+            const u32 tot = (u32)total;
+            const u32 per_warp = ((tot + DW - 1) / DW + 31u) & ~31u;
+            const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, tot);
+            Stream sa;
+            stream_init(sa, t, nrows, p0 + lane, p1);
+            while (sa.p < sa.end) {
+                stream_advance_row(sa, t);
+                const u32 j = sa.jbase + sa.p;
+                const u32 key = sa.ra + __ldg(a.B32 + j);  // rank - lo, below span
+                const u64 gc = __ldg(a.Bc + j);
+                // linear probing from a multiplicative hash of the rank
+                u32 h = (key * 2654435761u) >> (32 - HT_BITS);
+                bool done = false;
+                for (u32 probe = 0; probe < HT_PROBES; probe++) {
+                    const u32 k = keys[h];
+                    if (k == key) {
+                        done = true;
+                        break;
+                    }
+                    if (k == HEMPTY) {
+                        const u32 old = atomicCAS(&keys[h], HEMPTY, key);
+                        if (old == HEMPTY) atomicAdd(&s_count, 1u);
+                        if (old == HEMPTY || old == key) {
+                            done = true;
+                            break;
+                        }
+                    }
+                    h = (h + 1) & (HT - 1);
+                }
+                if (done) acc.add(h, sa.ca, gc);
+                else s_over = 1;
+                sa.p += 32;
+            }
+            __syncthreads();
+            if (tid == 0 && s_count > HT_LOAD) s_over = 1;
+            __syncthreads();
+        }
+        if (s_over) {
+            // abandoned: report it, clear the table for the next window
+            for (u32 x = tid; x < HT; x += DT) {
+                keys[x] = HEMPTY;
+                acc.zero(x);
+            }
+            if (tid == 0) a.ucount[wk] = HFAILED;
+            __syncthreads();
+            continue;
+        }
+        // emission: the occupied slots with non-zero values, sorted by rank
+        constexpr u32 PER = HT / DT;
+        u32 mine = 0;
+        u32 nzf = 0;
+#pragma unroll
+        for (u32 q = 0; q < PER; q++) {
+            const u32 x = tid * PER + q;
+            u64 v0, v1;
+            if (keys[x] != HEMPTY && acc.finalize(x, v0, v1)) {
+                nzf |= 1u << q;
+                mine++;
+            }
+        }
+        u64 nall;
+        u64 pos = block_exclusive_scan(mine, nall, ws);
+#pragma unroll
+        for (u32 q = 0; q < PER; q++) {
+            const u32 x = tid * PER + q;
+            if ((nzf >> q) & 1u) {
+                kA[pos] = keys[x];
+                iA[pos] = (uint16_t)x;
+                pos++;
+            }
+        }
+        __syncthreads();
+        const u32 n = (u32)nall;
+        block_sort_interval<DT, HT / DT>(kA, iA, kB, iB, n, 0, span ? span - 1 : 0, hist, ws);
+        const u64 obase = (u64)wk * HT;
+        for (u32 q = tid; q < n; q += DT) {
+            const u32 x = iA[q];
+            u64 v0, v1;
+            acc.take(x, v0, v1);
+            a.okey[obase + q] = rank_to_key(a.L, lo + kA[q]);
+            if (a.words == 1) {
+                a.ocoef[obase + q] = v0;
+            } else {
+                a.ocoef[2 * (obase + q)] = v0;
+                a.ocoef[2 * (obase + q) + 1] = v1;
+            }
+        }
+        __syncthreads();
+        for (u32 x = tid; x < HT; x += DT) {
+            keys[x] = HEMPTY;
+            acc.zero(x);
+        }
+        if (tid == 0) a.ucount[wk] = n;
+        __syncthreads();
+    }
+}
+
+// each finished window's terms to their place in the result (the windows'
+// scratch buffers differ by round, so a slice carries its source pointers)
+__global__ void k_hash_gather(const u64 *__restrict__ kptr, const u64 *__restrict__ cptr, const u64 *__restrict__ dst,
+                              const u64 *__restrict__ cnt, u32 nslices, u32 words, u64 *__restrict__ hkey,
+                              u64 *__restrict__ hcoef)
+{
+    for (u32 k = blockIdx.x; k < nslices; k += gridDim.x) {
+        const u64 *sk = (const u64 *)kptr[k], *sc = (const u64 *)cptr[k];
+        const u64 d0 = dst[k], n = cnt[k];
+        for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
+            hkey[d0 + t] = sk[t];
+            if (words == 1) {
+                hcoef[d0 + t] = sc[t];
+            } else {
+                hcoef[2 * (d0 + t)] = sc[2 * t];
+                hcoef[2 * (d0 + t) + 1] = sc[2 * t + 1];
+            }
+        }
+    }
+}
+
+// sort histogram: the bucket sort's 4096 words or, for its radix fallback,
+// 256 per warp
+constexpr u32 HT_HIST = BUCKETS > DW * 256 ? BUCKETS : DW * 256;
+
+constexpr size_t HASH_SMEM(u32 acc_bytes_)
+{
+    return (size_t)HT * 4 + (size_t)HT * acc_bytes_ + DTABLE_BYTES + (size_t)HT * (8 + 8 + 2 + 2) + HT_HIST * 4;
+}
+
+u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int requested, u64 lo, u64 end, u64 products,
+                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out)
+{
+    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
+    const int acc = acc_policy(kind, in.na < in.nb ? in.na : in.nb, requested);
+    // first windows: cost-balanced by term products (no window terms),
+    // about products / (HT 256) of them, at least 4 per SM; then no window
+    // wider than 2^31 ranks
+    u64 G0 = products / ((u64)HT * 256);
+    if (G0 < (u64)c.sm_count * 4) G0 = (u64)c.sm_count * 4;
+    if (G0 > end - lo) G0 = end - lo;
+    if (G0 > (1u << 20)) G0 = 1u << 20;
+    u32 l = 1;
+    while ((u64)(l + 1) * (l + 1) < 256ull * G0 && l < 4096) l++;
+    const u64 *gb = direct_groups(c, S, in.A, in.na, in.B, in.nb, lo, end, (u32)G0, l, products, 1u, 0u, 0u);
+    std::vector<u64> hgb(G0 + 1);
+    PM_CUDA(cudaMemcpyAsync(hgb.data(), gb, (G0 + 1) * 8, cudaMemcpyDeviceToHost, c.s));
+    c.sync();
+    std::vector<u64> wl, wh;
+    for (u64 g = 0; g < G0; g++) {
+        for (u64 x = hgb[g]; x < hgb[g + 1];) {
+            const u64 y = std::min(hgb[g + 1], x + (1ull << 31));
+            wl.push_back(x);
+            wh.push_back(y);
+            x = y;
+        }
+    }
+    struct Done {
+        u64 lo, n;
+        const u64 *k, *cf;
+    };
+    std::vector<Done> done;
+    u32 *E2 = S.get<u32>((size_t)c.sm_count * 2 * in.na);
+    const size_t smem = HASH_SMEM(acc_bytes(acc));
+    u32 rounds = 0;
+    while (!wl.empty()) {
+        if (++rounds > 40) throw Error(PM_ECUDA, "hash windows did not converge");
+        const u32 nw = (u32)wl.size();
+        u64 *dlo = S.get<u64>(nw), *dhi = S.get<u64>(nw), *cnt = S.get<u64>(nw);
+        u64 *skey = S.get<u64>((size_t)nw * HT), *scoef = S.get<u64>((size_t)nw * HT * words);
+        u32 *wnext = S.get<u32>(1);
+        PM_CUDA(cudaMemcpyAsync(dlo, wl.data(), nw * 8ull, cudaMemcpyHostToDevice, c.s));
+        PM_CUDA(cudaMemcpyAsync(dhi, wh.data(), nw * 8ull, cudaMemcpyHostToDevice, c.s));
+        PM_CUDA(cudaMemsetAsync(wnext, 0, 4, c.s));
+        HashArgs h;
+        memset(&h, 0, sizeof(h));
+        h.A = in.A;
+        h.Ac = in.Ac;
+        h.B = in.B;
+        h.Bc = in.Bc;
+        h.B32 = in.B32;
+        h.na = in.na;
+        h.nb = in.nb;
+        h.wlo = dlo;
+        h.whi = dhi;
+        h.nwin = nw;
+        h.E2 = E2;
+        h.okey = skey;
+        h.ocoef = scoef;
+        h.ucount = cnt;
+        h.wnext = wnext;
+        h.L = in.L;
+        h.words = words;
+        const unsigned grid = (unsigned)std::min<u64>(nw, (u64)c.sm_count);
+        if (acc == ACC_W64) {
+            set_smem(k_hash<ACC_W64>, smem);
+            k_hash<ACC_W64><<<grid, DT, smem, c.s>>>(h);
+        } else if (acc == ACC_L16) {
+            set_smem(k_hash<ACC_L16>, smem);
+            k_hash<ACC_L16><<<grid, DT, smem, c.s>>>(h);
+        } else {
+            set_smem(k_hash<ACC_I128>, smem);
+            k_hash<ACC_I128><<<grid, DT, smem, c.s>>>(h);
+        }
+        PM_LAUNCHED(c);
+        std::vector<u64> hc(nw);
+        PM_CUDA(cudaMemcpyAsync(hc.data(), cnt, nw * 8ull, cudaMemcpyDeviceToHost, c.s));
+        c.sync();
+        std::vector<u64> nl, nh;
+        for (u32 k = 0; k < nw; k++) {
+            if (hc[k] == HFAILED) {
+                if (wh[k] - wl[k] < 2) throw Error(PM_ECUDA, "hash window of one monomial overflowed");
+                const u64 mid = wl[k] + (wh[k] - wl[k]) / 2;
+                nl.push_back(wl[k]);
+                nh.push_back(mid);
+                nl.push_back(mid);
+                nh.push_back(wh[k]);
+            } else if (hc[k]) {
+                done.push_back(Done{wl[k], hc[k], skey + (size_t)k * HT, scoef + (size_t)k * HT * words});
+            }
+        }
+        wl.swap(nl);
+        wh.swap(nh);
+    }
+    if (rounds_out) *rounds_out = rounds;
+    // the windows in rank order, concatenated
+    std::sort(done.begin(), done.end(), [](const Done &x, const Done &y) { return x.lo < y.lo; });
+    u64 n_out = 0;
+    for (const Done &d : done) n_out += d.n;
+    if (n_out > cap || !hkey) return n_out;
+    const u32 ns = (u32)done.size();
+    std::vector<u64> src(ns), srcc(ns), dst(ns), cn(ns);
+    u64 run = 0;
+    for (u32 k = 0; k < ns; k++) {
+        src[k] = (u64)(uintptr_t)done[k].k;
+        srcc[k] = (u64)(uintptr_t)done[k].cf;
+        dst[k] = run;
+        cn[k] = done[k].n;
+        run += done[k].n;
+    }
+    u64 *dsrc = S.get<u64>(ns), *dsrcc = S.get<u64>(ns), *ddst = S.get<u64>(ns), *dcn = S.get<u64>(ns);
+    PM_CUDA(cudaMemcpyAsync(dsrc, src.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
+    PM_CUDA(cudaMemcpyAsync(dsrcc, srcc.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
+    PM_CUDA(cudaMemcpyAsync(ddst, dst.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
+    PM_CUDA(cudaMemcpyAsync(dcn, cn.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
+    if (ns) {
+        k_hash_gather<<<std::min<u32>(ns, 65535u), 256, 0, c.s>>>(dsrc, dsrcc, ddst, dcn, ns, words, hkey, hcoef);
+        PM_LAUNCHED(c);
+    }
+    c.sync();  // the host vectors above must outlive the copies
+    return n_out;
 }
 
 }  // namespace pm

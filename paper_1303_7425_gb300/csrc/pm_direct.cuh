@@ -29,6 +29,21 @@ struct DirectArgs {
     u64 nwin_max;        // bound on the window count (host), slices for compaction
 };
 
+// hashed windows (sparse results in large rank boxes): the canonical
+// operands and the product layout
+struct HashInputs {
+    const u64 *A, *Ac, *B, *Bc;  // ranks (sorted) and coefficients of f and g
+    const u32 *B32;              // low 32 bits of g's ranks
+    u32 na, nb;
+    Layout L;
+};
+// h = f * g over the rank interval [lo, end) with hashed windows: several
+// rounds (windows that overflow their table are split and run again), then
+// the windows' terms are gathered in rank order into hkey/hcoef when the
+// result fits `cap`.  Returns the result size; *rounds_out = rounds run.
+u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int requested, u64 lo, u64 end, u64 products,
+                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out);
+
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
 u32 direct_max_slots(int kind, u64 min_n, int requested);
 // G + 1 group boundaries over [lo, end) with about equal cost; win: the

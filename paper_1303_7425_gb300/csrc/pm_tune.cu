@@ -132,8 +132,9 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
         add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 20, 50000);
         add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 3, 5000);
     }
-    // sort + reduce: chunk sizes
+    // sort + reduce: chunk sizes; hashed windows
     for (u32 chunk : {2048u, 4096u}) add(PM_STRATEGY_SORT, 0, 0, PM_ACC_AUTO, chunk);
+    add(PM_STRATEGY_HASH, 0, 0, PM_ACC_AUTO, 0);
 
     pm_tune_report rep;
     memset(&rep, 0, sizeof(rep));

@@ -78,3 +78,16 @@ def check_canonical(keys, coefs, bits, kind="m61"):
         guard |= np.uint64(1 << (off + w - 1))
         off += w
     assert not np.any(keys & guard)
+
+
+def eval_pow2(exps, coefs, a):
+    """p(2^a_1, ..., 2^a_n) mod 2^61 - 1 for a polynomial with residue
+    coefficients: since 2^61 = 1 (mod 2^61 - 1), each term's value is its
+    coefficient rotated left by (a . e) mod 61 bits inside 61 bits."""
+    e = np.asarray(exps, dtype=np.uint64)
+    k = (e @ np.asarray(a, dtype=np.uint64)) % np.uint64(61)
+    c = np.asarray(coefs, dtype=np.uint64)
+    rot = ((c << k) & np.uint64(P61)) | (c >> (np.uint64(61) - k))
+    lo = int((rot & np.uint64((1 << 31) - 1)).sum(dtype=np.uint64))
+    hi = int((rot >> np.uint64(31)).sum(dtype=np.uint64))
+    return (lo + (hi << 31)) % P61

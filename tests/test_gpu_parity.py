@@ -231,6 +231,43 @@ def test_direct_rank_decoding_extents(bits, lims):
     assert_same(gpu, ref, bits)
 
 
+@pytest.mark.parametrize("case", ["c1", "dense_i64", "sparse3", "sparse5", "collisions"])
+def test_hash_strategy_exact(case):
+    """Hashed windows (PM_STRATEGY_HASH) on dense, sparse and colliding
+    products, both coefficient kinds: bit-exact with the oracle."""
+    if case == "c1":
+        w = polygen.workload_c1()
+    elif case == "dense_i64":
+        mons = polygen.monomials_total_degree(3, 10)
+        st = polygen.Stream(5, 1)
+        w = polygen.Workload("d3", 3, [12] * 3, "i64", polygen.Poly(mons, st.coef_i64(len(mons), 1 << 40)),
+                             polygen.Poly(mons[::-1].copy(), st.coef_i64(len(mons), 1 << 40)))
+    elif case == "sparse3":
+        w = polygen.sparse_product(polygen.Stream(8, 0), 3, 700, 500, 200)
+    elif case == "sparse5":
+        w = polygen.sparse_product(polygen.Stream(9, 0), 5, 1500, 900, 30)
+    else:
+        st = polygen.Stream(10, 0)
+        e = st.below(6, 800 * 3).astype(np.uint32).reshape(800, 3)
+        w = polygen.Workload("col", 3, [10] * 3, "m61", polygen.Poly(e, st.coef_m61(800)),
+                             polygen.Poly(e[::-1].copy(), st.coef_m61(800)))
+    ref = _oracle(w)
+    gpu = run_gpu(w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, strategy="hash")
+    assert gpu[2]["strategy"] == "hash"
+    assert_same(gpu, ref, w.field_bits)
+
+
+def test_hash_windows_split_when_full():
+    """4 million term products, nearly all distinct, over a box of 5e8 ranks:
+    the first windows (about 6,600 monomials each) overflow their tables,
+    are split over several rounds, and the result is still exact."""
+    w = polygen.sparse_product(polygen.Stream(12, 0), 3, 2000, 2000, 400)
+    ref = _oracle(w)
+    gpu = run_gpu(w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, strategy="hash")
+    assert gpu[2]["refine_rounds"] >= 2
+    assert_same(gpu, ref, w.field_bits)
+
+
 def test_int128_near_bound():
     a, b = -2**63, 2**63 - 1
     fe = np.array([[0], [1]], np.uint32)

@@ -391,3 +391,23 @@ def test_paper_example1_operands():
     # x^40 has coefficient 1, x y z t^37 has 40!/37! = 59280
     row = {tuple(e): int(c) for e, c in zip(w.f.exps.tolist(), w.f.coefs.tolist())}
     assert row[(40, 0, 0, 0)] == 1 and row[(1, 1, 1, 37)] == 40 * 39 * 38
+
+
+def test_eval_pow2_is_evaluation():
+    """The power-of-two evaluation used on full-size results agrees with the
+    oracle's plain evaluation (both mod 2^61 - 1)."""
+    from tests.gpu_util import eval_pow2
+    st = polygen.Stream(77, 0)
+    e = st.below(200, 500 * 4).astype(np.uint32).reshape(500, 4)
+    c = st.coef_m61(500)
+    for a in ([1, 2, 3, 4], [60, 59, 7, 33], [0, 0, 0, 0]):
+        assert eval_pow2(e, c, a) == oracle.evaluate(4, "m61", e, c, [pow(2, x, P61) for x in a])
+
+
+def test_paper_examples_2_3_operands():
+    """Sec. 6, Examples 2 and 3: the operands have C(30, 5) = 142,506 and
+    C(33, 5) = 237,336 terms, the counts the paper prints."""
+    for name, n in (("ex2", math.comb(30, 5)), ("ex3", math.comb(33, 5))):
+        w = polygen.paper_example(name)
+        assert w.f.n == w.g.n == n
+    assert math.comb(30, 5) == 142506 and math.comb(33, 5) == 237336
