@@ -121,7 +121,8 @@ typedef struct pm_stats {
     uint64_t n_f, n_g;         /* canonical operand sizes                         */
     uint64_t term_products;    /* n_f * n_g                                       */
     uint64_t n_out;            /* result terms                                    */
-    uint64_t n_ranges;         /* output key ranges (one CTA each)                */
+    uint64_t n_ranges;         /* output key ranges (one CTA each; hash: windows
+                                  run over all rounds)                            */
     uint64_t box;              /* output-exponent box size used for ranks          */
     int32_t strategy;          /* PM_STRATEGY_DIRECT, _SORT or _HASH              */
     uint32_t refine_rounds;    /* partition refinement rounds (sort); window

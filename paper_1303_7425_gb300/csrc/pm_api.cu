@@ -371,8 +371,10 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         u32 rounds = 0;
         if (st) PM_CUDA(cudaEventRecord(e0, c.s));
         if (st) PM_CUDA(cudaEventRecord(k0, c.s));
+        u64 windows = 0;
         const u64 n_out = hash_product(c, S, in, kind, o.accumulator, lo, end, products, (u64 *)h->keys,
-                                       (u64 *)h->coefs, h->cap, &rounds);
+                                       (u64 *)h->coefs, h->cap, &rounds, &windows);
+        stats.n_ranges = windows;
         if (st) PM_CUDA(cudaEventRecord(k1, c.s));
         if (st) PM_CUDA(cudaEventRecord(e1, c.s));
         stats.refine_rounds = rounds;

@@ -637,7 +637,7 @@ __global__ void k_group_bounds(const u64 *__restrict__ cw, u64 nbk, u32 G, u64 l
 }
 
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window)
+                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window, u64 nbk_max)
 {
     // cost model: a grid point of the pp-matrix stands for products / ng
     // term products; a bucket also carries its share of the window costs
@@ -648,7 +648,7 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
     const u64 ng = (u64)R * Cc + Cc + R;
     const u64 span = end - lo;
-    const u64 nbk = span < 65536 ? span : 65536;
+    const u64 nbk = span < nbk_max ? span : nbk_max;
     const u64 bw = (span + nbk - 1) / nbk;
     u64 *hist = S.get<u64>(nbk), *cw = S.get<u64>(nbk + 1);
     PM_CUDA(cudaMemsetAsync(hist, 0, nbk * 8, c.s));
@@ -780,16 +780,17 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 //
 // A direct-addressed window holds one slot per rank, so a sparse box needs
 // so many windows that the FindEdge table (a row per window) and the row
-// staging per window explode.  Here a window may span up to 2^32 ranks; its
+// staging per window explode.  Here a window may span up to 2^31 ranks; its
 // distinct result monomials go to a shared-memory hash table (HT slots,
 // linear probing, bounded), and FindEdge is done inside the kernel: for the
 // window's two boundaries each thread walks a staircase over a contiguous
 // chunk of rows (the row edges fall as the row rises, Sec. 2) and leaves the
-// column range of every row in a per-CTA scratch.  Emission sorts the
+// column range of every row in a per-CTA scratch; then each thread inserts
+// the products of rows tid, tid + 1024, ... directly.  Emission sorts the
 // occupied slots by rank (block_sort_interval) and writes the window's
 // terms in order.  A window with more than HT_LOAD distinct monomials (or a
 // probe run longer than HT_PROBES) is abandoned and reported; the host
-// splits it in two and runs the halves in the next round.
+// splits it in four and runs the parts in the next round.
 // ---------------------------------------------------------------------------
 
 constexpr u32 HT = 4096, HT_BITS = 12;
@@ -823,8 +824,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
     u32 *keys = (u32 *)smem;
     HA acc;
     acc.carve(smem + HT * 4);
-    DTables t = carve_dtables(smem + HT * 4 + (size_t)HT * HA::bytes);
-    unsigned char *sb_ = smem + HT * 4 + (size_t)HT * HA::bytes + DTABLE_BYTES;
+    unsigned char *sb_ = smem + HT * 4 + (size_t)HT * HA::bytes;
     u64 *kA = (u64 *)sb_, *kB = kA + HT;
     uint16_t *iA = (uint16_t *)(kB + HT), *iB = iA + HT;
     u32 *hist = (u32 *)(iB + HT);  // HT_HIST words
@@ -873,32 +873,19 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
             }
         }
         __syncthreads();
-        for (u32 base = i0; base < i1 && !s_over; base += DROWS) {
-            const u32 i = base + tid;
-            u32 jl = 0, len = 0, ra = 0;
-            u64 ca = 0;
-            if (i < i1) {
-                jl = E2[2 * (i - i0)];
-                len = E2[2 * (i - i0) + 1] - jl;
-                ra = (u32)a.A[i] - (u32)lo;
-                ca = a.Ac[i];
-            }
-            u64 total;
-            const u64 ex = block_exclusive_scan(len, total, ws);
-            t.off[tid] = (u32)ex;
-            t.rec[tid] = make_uint4((u32)ca, (u32)(ca >> 32), ra, jl - (u32)ex);
-            if (tid == 0) t.off[DROWS] = (u32)total;
-            const u32 nrows = min(i1 - base, (u32)DROWS);
-            __syncthreads();
-            const u32 tot = (u32)total;
-            const u32 per_warp = ((tot + DW - 1) / DW + 31u) & ~31u;
-            const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, tot);
-            Stream sa;
-            stream_init(sa, t, nrows, p0 + lane, p1);
-            while (sa.p < sa.end) {
-                stream_advance_row(sa, t);
-                const u32 j = sa.jbase + sa.p;
-                const u32 key = sa.ra + __ldg(a.B32 + j);  // rank - lo, below span
+        // the products: each thread takes rows i0 + tid, i0 + tid + DT, ...
+        // and inserts its row's products (a window in a sparse box has few
+        // products per row, so staging rows through shared memory and
+        // balancing them across the block costs more than it saves)
+        const volatile u32 *over = &s_over;
+        for (u32 i = i0 + tid; i < i1; i += DT) {
+            if (*over) break;
+            const u32 jl = E2[2 * (i - i0)], jh = E2[2 * (i - i0) + 1];
+            if (jh <= jl) continue;
+            const u32 ra = (u32)a.A[i] - (u32)lo;
+            const u64 ca = a.Ac[i];
+            for (u32 j = jl; j < jh; j++) {
+                const u32 key = ra + __ldg(a.B32 + j);  // rank - lo, below span
                 const u64 gc = __ldg(a.Bc + j);
                 // linear probing from a multiplicative hash of the rank
                 u32 h = (key * 2654435761u) >> (32 - HT_BITS);
@@ -911,7 +898,9 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
                     }
                     if (k == HEMPTY) {
                         const u32 old = atomicCAS(&keys[h], HEMPTY, key);
-                        if (old == HEMPTY) atomicAdd(&s_count, 1u);
+                        if (old == HEMPTY) {
+                            if (atomicAdd(&s_count, 1u) >= HT_LOAD) s_over = 1;
+                        }
                         if (old == HEMPTY || old == key) {
                             done = true;
                             break;
@@ -919,14 +908,15 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
                     }
                     h = (h + 1) & (HT - 1);
                 }
-                if (done) acc.add(h, sa.ca, gc);
-                else s_over = 1;
-                sa.p += 32;
+                if (done) {
+                    acc.add(h, ca, gc);
+                } else {
+                    s_over = 1;
+                    break;
+                }
             }
-            __syncthreads();
-            if (tid == 0 && s_count > HT_LOAD) s_over = 1;
-            __syncthreads();
         }
+        __syncthreads();
         if (s_over) {
             // abandoned: report it, clear the table for the next window
             for (u32 x = tid; x < HT; x += DT) {
@@ -1014,11 +1004,11 @@ constexpr u32 HT_HIST = BUCKETS > DW * 256 ? BUCKETS : DW * 256;
 
 constexpr size_t HASH_SMEM(u32 acc_bytes_)
 {
-    return (size_t)HT * 4 + (size_t)HT * acc_bytes_ + DTABLE_BYTES + (size_t)HT * (8 + 8 + 2 + 2) + HT_HIST * 4;
+    return (size_t)HT * 4 + (size_t)HT * acc_bytes_ + (size_t)HT * (8 + 8 + 2 + 2) + HT_HIST * 4;
 }
 
 u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int requested, u64 lo, u64 end, u64 products,
-                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out)
+                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out, u64 *windows_out)
 {
     const u32 words = kind == PM_COEF_M61 ? 1 : 2;
     const int acc = acc_policy(kind, in.na < in.nb ? in.na : in.nb, requested);
@@ -1031,7 +1021,8 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     if (G0 > (1u << 20)) G0 = 1u << 20;
     u32 l = 1;
     while ((u64)(l + 1) * (l + 1) < 256ull * G0 && l < 4096) l++;
-    const u64 *gb = direct_groups(c, S, in.A, in.na, in.B, in.nb, lo, end, (u32)G0, l, products, 1u, 0u, 0u);
+    const u64 *gb = direct_groups(c, S, in.A, in.na, in.B, in.nb, lo, end, (u32)G0, l, products, 1u, 0u, 0u,
+                                  1ull << 20);
     std::vector<u64> hgb(G0 + 1);
     PM_CUDA(cudaMemcpyAsync(hgb.data(), gb, (G0 + 1) * 8, cudaMemcpyDeviceToHost, c.s));
     c.sync();
@@ -1055,6 +1046,7 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     while (!wl.empty()) {
         if (++rounds > 40) throw Error(PM_ECUDA, "hash windows did not converge");
         const u32 nw = (u32)wl.size();
+        if (windows_out) *windows_out += nw;
         u64 *dlo = S.get<u64>(nw), *dhi = S.get<u64>(nw), *cnt = S.get<u64>(nw);
         u64 *skey = S.get<u64>((size_t)nw * HT), *scoef = S.get<u64>((size_t)nw * HT * words);
         u32 *wnext = S.get<u32>(1);
@@ -1098,12 +1090,14 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         std::vector<u64> nl, nh;
         for (u32 k = 0; k < nw; k++) {
             if (hc[k] == HFAILED) {
-                if (wh[k] - wl[k] < 2) throw Error(PM_ECUDA, "hash window of one monomial overflowed");
-                const u64 mid = wl[k] + (wh[k] - wl[k]) / 2;
-                nl.push_back(wl[k]);
-                nh.push_back(mid);
-                nl.push_back(mid);
-                nh.push_back(wh[k]);
+                // four parts of equal rank width (fewer when narrower)
+                const u64 span = wh[k] - wl[k];
+                if (span < 2) throw Error(PM_ECUDA, "hash window of one monomial overflowed");
+                const u64 parts = span < 4 ? span : 4;
+                for (u64 q = 0; q < parts; q++) {
+                    nl.push_back(wl[k] + span * q / parts);
+                    nh.push_back(wl[k] + span * (q + 1) / parts);
+                }
             } else if (hc[k]) {
                 done.push_back(Done{wl[k], hc[k], skey + (size_t)k * HT, scoef + (size_t)k * HT * words});
             }

@@ -40,9 +40,10 @@ struct HashInputs {
 // h = f * g over the rank interval [lo, end) with hashed windows: several
 // rounds (windows that overflow their table are split and run again), then
 // the windows' terms are gathered in rank order into hkey/hcoef when the
-// result fits `cap`.  Returns the result size; *rounds_out = rounds run.
+// result fits `cap`.  Returns the result size; *rounds_out = rounds run,
+// *windows_out += windows run over all rounds.
 u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int requested, u64 lo, u64 end, u64 products,
-                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out);
+                 u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out, u64 *windows_out);
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested);
 u32 direct_max_slots(int kind, u64 min_n, int requested);
@@ -50,7 +51,7 @@ u32 direct_max_slots(int kind, u64 min_n, int requested);
 // window width (slots) the accumulate kernel will use; a group costs
 // products + cost_row (rows staged) + cost_window (windows)
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
-                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window);
+                   u32 grid_l, u64 products, u32 win, u32 cost_row, u32 cost_window, u64 nbk_max = 65536);
 // Windows, FindEdge and the accumulate kernel.  On return a.W (window
 // starts), a.ucount (terms per window) and a.nwin_max describe the result
 // slices: window k's terms sit at a.W[k] - a.lo in the output scratch.
