@@ -27,7 +27,14 @@
  *                      results in [0, p), p = 2^61 - 1.
  *   PM_COEF_I64_ACC128 int64 inputs, exact results as int128 stored as two
  *                      uint64 words per term (low word first, two's
- *                      complement).
+ *                      complement); products whose int128 bound rule fails
+ *                      are refused (PM_ECOEF_BOUND).
+ *   PM_COEF_I64_ACC192 int64 inputs, exact results as 192-bit integers,
+ *                      three uint64 words per term (low word first, two's
+ *                      complement): a sum of at most 2^31 products of
+ *                      magnitude <= 2^126 always fits, so no bound rule
+ *                      applies (the batched and no-allocation entry points
+ *                      do not take this kind).
  *
  * Input conventions: terms in any order; a repeated monomial's coefficients
  * are summed; zero coefficients are dropped.  The result never holds a zero
@@ -67,11 +74,12 @@ typedef struct pm_packing {
 
 typedef enum pm_coef_kind {
     PM_COEF_M61 = 0,
-    PM_COEF_I64_ACC128 = 1
+    PM_COEF_I64_ACC128 = 1,
+    PM_COEF_I64_ACC192 = 2
 } pm_coef_kind;
 
 /* Input terms (device): exps is n x nvars uint32, row-major; coefs is n
- * uint64 (M61) or n int64 (I64_ACC128).  n < 2^31. */
+ * uint64 (M61) or n int64 (I64 kinds).  n < 2^31. */
 typedef struct pm_terms_in {
     const uint32_t *exps;
     const void *coefs;

@@ -1,4 +1,5 @@
-"""Python access to the C oracle (oracle.c).
+"""Python access to the C oracle (oracle.c), and the exact-integer product
+(exact.py) for the 192-bit kind.
 
 TEST INFRASTRUCTURE ONLY: the tests, the package's smoke check and the
 benchmark's CPU-baseline leg use this module; the library never does.  This
@@ -13,6 +14,8 @@ import subprocess
 from typing import Optional, Sequence, Tuple
 
 import numpy as np
+
+from .exact import ExactError, mul_exact, words192  # noqa: F401
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.c")

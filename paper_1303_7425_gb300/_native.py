@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libpolymul.so")
 PM_MAX_VARS = 16
 PM_OK, PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND = 0, -1, -2, -3
 PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA, PM_EPLAN = -4, -5, -6, -7, -8
-KIND = {"m61": 0, "i64": 1}
+KIND = {"m61": 0, "i64": 1, "i192": 2}
 STRATEGY = {"auto": 0, "direct": 1, "sort": 2, "hash": 3}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
 ACCUMULATOR = {"auto": 0, "wide": 1, "limbs": 2}
@@ -152,7 +152,7 @@ def _check_cuda(*tensors):
 @dataclass
 class Product:
     keys: "object"            # (n,) int64 tensor holding uint64 packed keys
-    coefs: "object"           # (n,) int64 tensor of residues, or (n, 2) int128 (lo, hi) words
+    coefs: "object"           # (n,) int64 residues, or (n, 2) int128 / (n, 3) int192 words, low word first
     n: int
     stats: dict
 
@@ -180,14 +180,14 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
     from pm_out_bound."""
     import torch
     _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
-    words = 1 if kind == "m61" else 2
+    words = {"m61": 1, "i64": 2, "i192": 3}[kind]
     pk = packing(field_bits)
     f = _terms_in(f_exps, f_coefs)
     g = _terms_in(g_exps, g_coefs)
     if out is None:
         cap = out_bound(field_bits, f_exps, g_exps, stream)
         keys = torch.empty(max(cap, 1), dtype=torch.int64, device=f_exps.device)
-        coefs = torch.empty((max(cap, 1), 2) if words == 2 else (max(cap, 1),), dtype=torch.int64,
+        coefs = torch.empty((max(cap, 1), words) if words > 1 else (max(cap, 1),), dtype=torch.int64,
                             device=f_exps.device)
     else:
         keys, coefs = out
@@ -612,9 +612,10 @@ def autotune(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61", st
                               C.POINTER(pm_terms_out), C.POINTER(pm_options), C.POINTER(pm_tune_report), C.c_void_p]
     L.pm_autotune.restype = C.c_int
     cap = out_bound(field_bits, f_exps, g_exps, stream)
-    words = 1 if kind == "m61" else 2
+    words = {"m61": 1, "i64": 2, "i192": 3}[kind]
     keys = torch.empty(max(cap, 1), dtype=torch.int64, device=f_exps.device)
-    coefs = torch.empty((max(cap, 1), 2) if words == 2 else (max(cap, 1),), dtype=torch.int64, device=f_exps.device)
+    coefs = torch.empty((max(cap, 1), words) if words > 1 else (max(cap, 1),), dtype=torch.int64,
+                        device=f_exps.device)
     h = pm_terms_out(keys.data_ptr(), coefs.data_ptr(), 0, cap)
     best = pm_options()
     rep = pm_tune_report()

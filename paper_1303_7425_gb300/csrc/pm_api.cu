@@ -196,12 +196,7 @@ __global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__rest
         const u64 src = base[k] - base0, dst = foff[k], n = ucount[k];
         for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
             hkey[dst + t] = skey[src + t];
-            if (words == 1) {
-                hcoef[dst + t] = scoef[src + t];
-            } else {
-                hcoef[2 * (dst + t)] = scoef[2 * (src + t)];
-                hcoef[2 * (dst + t) + 1] = scoef[2 * (src + t) + 1];
-            }
+            for (u32 q = 0; q < words; q++) hcoef[words * (dst + t) + q] = scoef[words * (src + t) + q];
         }
     }
 }
@@ -213,7 +208,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     const bool capture = rec && rec->mode == PlanRec::CAPTURE;
     const u32 *abort = capture ? rec->d_flag : nullptr;
     validate_packing(pk);
-    if (kind != PM_COEF_M61 && kind != PM_COEF_I64_ACC128) throw Error(PM_EINVAL, "bad coefficient kind");
+    if (kind != PM_COEF_M61 && kind != PM_COEF_I64_ACC128 && kind != PM_COEF_I64_ACC192)
+        throw Error(PM_EINVAL, "bad coefficient kind");
     validate_terms(f);
     validate_terms(g);
     if (!h) throw Error(PM_EINVAL, "null output");
@@ -304,7 +300,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     const u64 products = F.n * G.n;
     stats.term_products = products;
     stats.box = box;
-    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
+    const u32 words = kind == PM_COEF_M61 ? 1 : (kind == PM_COEF_I64_ACC192 ? 3 : 2);
 
     // strategy choice (autotuner defaults)
     int strategy = o.strategy;

@@ -77,6 +77,26 @@ __device__ __forceinline__ void add128(u64 &lo, u64 &hi, u64 blo, u64 bhi)
     lo = l;
 }
 
+// (w0, w1, w2) += (x0, x1, x2), 192-bit two's complement words
+__device__ __forceinline__ void add192w(u64 &w0, u64 &w1, u64 &w2, u64 x0, u64 x1, u64 x2)
+{
+    const u64 l = w0 + x0;
+    const u64 c0 = l < w0 ? 1ull : 0ull;
+    const u64 t = x1 + c0;                   // may wrap: then it carries one more
+    const u64 c1a = t < x1 ? 1ull : 0ull;
+    const u64 m = w1 + t;
+    const u64 c1b = m < w1 ? 1ull : 0ull;
+    w0 = l;
+    w1 = m;
+    w2 = w2 + x2 + c1a + c1b;
+}
+
+// (w0, w1, w2) += the int128 (blo, bhi) sign-extended to 192 bits
+__device__ __forceinline__ void add192(u64 &w0, u64 &w1, u64 &w2, u64 blo, u64 bhi)
+{
+    add192w(w0, w1, w2, blo, bhi, (u64)((i64)bhi >> 63));
+}
+
 // ---------------------------------------------------------------------------
 // block-wide exclusive scan (all threads of the block must call it)
 // ---------------------------------------------------------------------------

@@ -234,16 +234,19 @@ __device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t)
 //            value); exact while a slot receives at most 65537 products,
 //            i.e. when min(n_f, n_g) <= 65537 (one product per row and
 //            per column at most), 16 bytes per slot;
-//   ACC_I128: int64 inputs; 128-bit sum as lo and hi words, 16 bytes.
+//   ACC_I128: int64 inputs; 128-bit sum as lo and hi words, 16 bytes;
+//   ACC_I192: int64 inputs; 192-bit sum in three words, each word's atomic
+//            add returning the carry into the next, 24 bytes.
 // ---------------------------------------------------------------------------
-enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2 };
+enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2, ACC_I192 = 3 };
 
 template <int ACC, u32 STRIDE = 0>
 struct Acc {
-    static constexpr u32 bytes = ACC == ACC_W64 ? 12 : 16;
+    static constexpr u32 bytes = ACC == ACC_W64 ? 12 : (ACC == ACC_I192 ? 24 : 16);
+    static constexpr u32 words = ACC == ACC_I192 ? 3 : (ACC == ACC_I128 ? 2 : 1);  // result words
     // array stride (a window may use fewer slots)
     static constexpr u32 slots = STRIDE ? STRIDE : acc_stride(bytes);
-    u64 *w;      // ACC_W64: sums; ACC_I128: lo words [0, slots), hi words [slots, 2 slots)
+    u64 *w;      // ACC_W64: sums; ACC_I128/I192: word k of slot s at w[k * slots + s]
     u32 *c;      // ACC_W64: wrap counts; ACC_L16: limb counters, limb k at [k * slots, (k+1) * slots)
 
     __device__ __forceinline__ void carve(unsigned char *p)
@@ -264,6 +267,7 @@ struct Acc {
         } else {
             w[s] = 0;
             w[slots + s] = 0;
+            if (ACC == ACC_I192) w[2 * slots + s] = 0;
         }
     }
     __device__ __forceinline__ void add(u32 s, u64 a, u64 b)
@@ -278,20 +282,33 @@ struct Acc {
             atomicAdd(&c[slots + s], (u32)(v >> 16) & 0xFFFFu);
             atomicAdd(&c[2 * slots + s], (u32)(v >> 32) & 0xFFFFu);
             atomicAdd(&c[3 * slots + s], (u32)(v >> 48));
-        } else {
+        } else if (ACC == ACC_I128) {
             u64 plo, phi;
             mul_i64_wide((i64)a, (i64)b, plo, phi);
             const u64 old = atomicAdd(&w[s], plo);
             atomicAdd(&w[slots + s], phi + (old + plo < old ? 1ull : 0ull));
+        } else {
+            // the product sign-extended to 192 bits, word by word; each
+            // atomic add's carry (from the value it returns) goes to the
+            // next word, so the three words hold the exact sum
+            u64 plo, phi;
+            mul_i64_wide((i64)a, (i64)b, plo, phi);
+            const u64 ext = (u64)((i64)phi >> 63);
+            const u64 o0 = atomicAdd(&w[s], plo);
+            const u64 t = phi + (o0 + plo < o0 ? 1ull : 0ull);
+            const u64 c1a = t < phi ? 1ull : 0ull;
+            const u64 o1 = atomicAdd(&w[slots + s], t);
+            const u64 c1b = o1 + t < o1 ? 1ull : 0ull;
+            atomicAdd(&w[2 * slots + s], ext + c1a + c1b);
         }
     }
-    // emission, first pass: the slot's value (residue mod p with v1 = 0, or
-    // the int128 (v0, v1)), left in the slot in a form take() reads back
-    // with fewer loads: a residue as two 32-bit words in the first two
-    // arrays (ACC_L16) or as the whole sum (ACC_W64)
-    __device__ __forceinline__ bool finalize(u32 s, u64 &v0, u64 &v1)
+    // emission, first pass: the slot's value (a residue mod p in v0, or the
+    // two's complement words v0, v1, v2), left in the slot in a form take()
+    // reads back with fewer loads: a residue as two 32-bit words in the
+    // first two arrays (ACC_L16) or as the whole sum (ACC_W64)
+    __device__ __forceinline__ bool finalize(u32 s, u64 &v0, u64 &v1, u64 &v2)
     {
-        const bool nz = value(s, v0, v1);
+        const bool nz = value(s, v0, v1, v2);
         if (ACC == ACC_W64) {
             w[s] = v0;
             c[s] = 0;
@@ -305,15 +322,15 @@ struct Acc {
     }
     // emission, second pass: the value finalize() left, and the slot cleared
     // for the next window
-    __device__ __forceinline__ void take(u32 s, u64 &v0, u64 &v1)
+    __device__ __forceinline__ void take(u32 s, u64 &v0, u64 &v1, u64 &v2)
     {
+        v1 = 0;
+        v2 = 0;
         if (ACC == ACC_W64) {
             v0 = w[s];
-            v1 = 0;
             w[s] = 0;
         } else if (ACC == ACC_L16) {
             v0 = (u64)c[s] | ((u64)c[slots + s] << 32);
-            v1 = 0;
             c[s] = 0;
             c[slots + s] = 0;
         } else {
@@ -321,14 +338,19 @@ struct Acc {
             v1 = w[slots + s];
             w[s] = 0;
             w[slots + s] = 0;
+            if (ACC == ACC_I192) {
+                v2 = w[2 * slots + s];
+                w[2 * slots + s] = 0;
+            }
         }
     }
-    // the slot's value: residue mod p (v1 = 0), or the int128 (v0, v1)
-    __device__ __forceinline__ bool value(u32 s, u64 &v0, u64 &v1) const
+    // the slot's value: residue mod p (v1 = v2 = 0), or the integer's words
+    __device__ __forceinline__ bool value(u32 s, u64 &v0, u64 &v1, u64 &v2) const
     {
+        v1 = 0;
+        v2 = 0;
         if (ACC == ACC_W64) {
             v0 = m61_reduce(m61_reduce(w[s]) + 8ull * c[s]);
-            v1 = 0;
             return v0 != 0;
         } else if (ACC == ACC_L16) {
             // sum = L0 + L1 2^16 + L2 2^32 + L3 2^48 with L_k < 2^32
@@ -339,12 +361,12 @@ struct Acc {
             add128(lo, hi, l3 << 48, l3 >> 16);
             // 2^64 = 8 (mod p); hi < 2^17
             v0 = m61_reduce(m61_reduce(lo) + 8ull * hi);
-            v1 = 0;
             return v0 != 0;
         } else {
             v0 = w[s];
             v1 = w[slots + s];
-            return (v0 | v1) != 0;
+            if (ACC == ACC_I192) v2 = w[2 * slots + s];
+            return (v0 | v1 | v2) != 0;
         }
     }
 };
@@ -469,8 +491,8 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         for (u32 sb = s0; sb < s1; sb += 32) {
             const u32 s = sb + lane;
             bool nz = false;
-            u64 x0, x1;
-            if (s < s1) nz = acc.finalize(s, x0, x1);
+            u64 x0, x1, x2;
+            if (s < s1) nz = acc.finalize(s, x0, x1, x2);
             wcount += __popc(__ballot_sync(0xffffffffu, nz));
         }
         u64 wtot;
@@ -480,19 +502,17 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         u64 put = (lo - a.lo) + __shfl_sync(0xffffffffu, wbase, 0);
         for (u32 sb = s0; sb < s1; sb += 32) {
             const u32 s = sb + lane;
-            u64 v0 = 0, v1 = 0;
-            if (s < s1) acc.take(s, v0, v1);
-            const bool nz = (v0 | v1) != 0;
+            u64 v0 = 0, v1 = 0, v2 = 0;
+            if (s < s1) acc.take(s, v0, v1, v2);
+            const bool nz = (v0 | v1 | v2) != 0;
             const u32 bal = __ballot_sync(0xffffffffu, nz);
             if (nz) {
                 const u64 d = put + __popc(bal & ((1u << lane) - 1u));
                 a.okey[d] = rank_to_key(a.L, lo + s);
-                if (ACC != ACC_I128) {
-                    a.ocoef[d] = v0;
-                } else {
-                    a.ocoef[2 * d] = v0;
-                    a.ocoef[2 * d + 1] = v1;
-                }
+                constexpr u32 W = Acc<ACC>::words;
+                a.ocoef[W * d] = v0;
+                if (W > 1) a.ocoef[W * d + 1] = v1;
+                if (W > 2) a.ocoef[W * d + 2] = v2;
             }
             put += __popc(bal);
         }
@@ -676,6 +696,7 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
 
 static int acc_policy(int kind, u64 min_n, int requested)
 {
+    if (kind == PM_COEF_I64_ACC192) return ACC_I192;
     if (kind != PM_COEF_M61) return ACC_I128;
     if (requested == PM_ACC_WIDE) return ACC_W64;
     if (requested == PM_ACC_LIMBS) {
@@ -685,7 +706,7 @@ static int acc_policy(int kind, u64 min_n, int requested)
     return min_n <= 65537 ? ACC_L16 : ACC_W64;
 }
 
-static u32 acc_bytes(int acc) { return acc == ACC_W64 ? 12 : 16; }
+static u32 acc_bytes(int acc) { return acc == ACC_W64 ? 12 : (acc == ACC_I192 ? 24 : 16); }
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested)
 {
@@ -767,9 +788,12 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     } else if (acc == ACC_L16) {
         set_smem(k_direct<ACC_L16>, bytes);
         k_direct<ACC_L16><<<grid, DT, bytes, c.s>>>(a, slots);
-    } else {
+    } else if (acc == ACC_I128) {
         set_smem(k_direct<ACC_I128>, bytes);
         k_direct<ACC_I128><<<grid, DT, bytes, c.s>>>(a, slots);
+    } else {
+        set_smem(k_direct<ACC_I192>, bytes);
+        k_direct<ACC_I192><<<grid, DT, bytes, c.s>>>(a, slots);
     }
     PM_LAUNCHED(c);
     if (ev_k1) PM_CUDA(cudaEventRecord(ev_k1, c.s));
@@ -934,8 +958,8 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
 #pragma unroll
         for (u32 q = 0; q < PER; q++) {
             const u32 x = tid * PER + q;
-            u64 v0, v1;
-            if (keys[x] != HEMPTY && acc.finalize(x, v0, v1)) {
+            u64 v0, v1, v2;
+            if (keys[x] != HEMPTY && acc.finalize(x, v0, v1, v2)) {
                 nzf |= 1u << q;
                 mine++;
             }
@@ -957,15 +981,13 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         const u64 obase = (u64)wk * HT;
         for (u32 q = tid; q < n; q += DT) {
             const u32 x = iA[q];
-            u64 v0, v1;
-            acc.take(x, v0, v1);
+            u64 v0, v1, v2;
+            acc.take(x, v0, v1, v2);
             a.okey[obase + q] = rank_to_key(a.L, lo + kA[q]);
-            if (a.words == 1) {
-                a.ocoef[obase + q] = v0;
-            } else {
-                a.ocoef[2 * (obase + q)] = v0;
-                a.ocoef[2 * (obase + q) + 1] = v1;
-            }
+            constexpr u32 W = HA::words;
+            a.ocoef[W * (obase + q)] = v0;
+            if (W > 1) a.ocoef[W * (obase + q) + 1] = v1;
+            if (W > 2) a.ocoef[W * (obase + q) + 2] = v2;
         }
         __syncthreads();
         for (u32 x = tid; x < HT; x += DT) {
@@ -988,12 +1010,7 @@ __global__ void k_hash_gather(const u64 *__restrict__ kptr, const u64 *__restric
         const u64 d0 = dst[k], n = cnt[k];
         for (u64 t = threadIdx.x; t < n; t += blockDim.x) {
             hkey[d0 + t] = sk[t];
-            if (words == 1) {
-                hcoef[d0 + t] = sc[t];
-            } else {
-                hcoef[2 * (d0 + t)] = sc[2 * t];
-                hcoef[2 * (d0 + t) + 1] = sc[2 * t + 1];
-            }
+            for (u32 q = 0; q < words; q++) hcoef[words * (d0 + t) + q] = sc[words * t + q];
         }
     }
 }
@@ -1010,7 +1027,7 @@ constexpr size_t HASH_SMEM(u32 acc_bytes_)
 u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int requested, u64 lo, u64 end, u64 products,
                  u64 *hkey, u64 *hcoef, u64 cap, u32 *rounds_out, u64 *windows_out)
 {
-    const u32 words = kind == PM_COEF_M61 ? 1 : 2;
+    const u32 words = kind == PM_COEF_M61 ? 1 : (kind == PM_COEF_I64_ACC192 ? 3 : 2);
     const int acc = acc_policy(kind, in.na < in.nb ? in.na : in.nb, requested);
     // first windows: cost-balanced by term products (no window terms),
     // about products / (HT 256) of them, at least 4 per SM; then no window
@@ -1079,9 +1096,12 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         } else if (acc == ACC_L16) {
             set_smem(k_hash<ACC_L16>, smem);
             k_hash<ACC_L16><<<grid, DT, smem, c.s>>>(h);
-        } else {
+        } else if (acc == ACC_I128) {
             set_smem(k_hash<ACC_I128>, smem);
             k_hash<ACC_I128><<<grid, DT, smem, c.s>>>(h);
+        } else {
+            set_smem(k_hash<ACC_I192>, smem);
+            k_hash<ACC_I192><<<grid, DT, smem, c.s>>>(h);
         }
         PM_LAUNCHED(c);
         std::vector<u64> hc(nw);

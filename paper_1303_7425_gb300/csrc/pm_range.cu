@@ -142,7 +142,9 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
     __shared__ u32 win[2];
-    __shared__ u64 red[2 * RK_WARPS];
+    __shared__ u64 red[3 * RK_WARPS];
+    constexpr bool W3 = KIND == PM_COEF_I64_ACC192;        // 192-bit sums
+    constexpr u32 OW = KIND == PM_COEF_M61 ? 1 : (W3 ? 3 : 2);  // result words
     const size_t sort_bytes = (size_t)chunk * 8 * (KIND == PM_COEF_M61 ? 3 : 4) + RK_WARPS * 256 * 4 +
                               (size_t)chunk * 4;
     RowTables t = carve_rows(smem + ((sort_bytes + 15) & ~(size_t)15));
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
         if (O > chunk) {
             // a single monomial with more products than the chunk: plain sum
             if (hi - lo != 1 && tid == 0) atomicOr(a.status, ST_INTERNAL);
-            u64 s0 = 0, s1 = 0;
+            u64 s0 = 0, s1 = 0, s2 = 0;
             for (u32 base = i0; base < i1; base += ROWS) {
                 u32 nrows;
                 u32 total = stage_rows(a, t, base, i1, lo, hi, ws, nrows);
@@ -170,39 +172,41 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
                     } else {
                         u64 plo, phi;
                         mul_i64_wide((i64)t.rcoef[r], (i64)__ldg(a.gcoef + j), plo, phi);
-                        add128(s0, s1, plo, phi);
+                        if (W3) add192(s0, s1, s2, plo, phi);
+                        else add128(s0, s1, plo, phi);
                     }
                 });
                 __syncthreads();
             }
-            // block reduction of (s0, s1)
+            // block reduction of (s0, s1, s2)
             const u32 lane = tid & 31, w = tid >> 5;
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) {
                 u64 o0 = __shfl_down_sync(0xffffffffu, s0, d), o1 = __shfl_down_sync(0xffffffffu, s1, d);
+                u64 o2 = __shfl_down_sync(0xffffffffu, s2, d);
                 if (KIND == PM_COEF_M61) s0 = m61_add(s0, o0);
+                else if (W3) add192w(s0, s1, s2, o0, o1, o2);
                 else add128(s0, s1, o0, o1);
             }
             if (lane == 0) {
-                red[2 * w] = s0;
-                red[2 * w + 1] = s1;
+                red[3 * w] = s0;
+                red[3 * w + 1] = s1;
+                red[3 * w + 2] = s2;
             }
             __syncthreads();
             if (tid == 0) {
-                u64 r0 = 0, r1 = 0;
+                u64 r0 = 0, r1 = 0, r2 = 0;
                 for (int ww = 0; ww < RK_WARPS; ww++) {
-                    if (KIND == PM_COEF_M61) r0 = m61_add(r0, red[2 * ww]);
-                    else add128(r0, r1, red[2 * ww], red[2 * ww + 1]);
+                    if (KIND == PM_COEF_M61) r0 = m61_add(r0, red[3 * ww]);
+                    else if (W3) add192w(r0, r1, r2, red[3 * ww], red[3 * ww + 1], red[3 * ww + 2]);
+                    else add128(r0, r1, red[3 * ww], red[3 * ww + 1]);
                 }
                 u64 cnt = 0;
-                if ((r0 | r1) != 0) {
+                if ((r0 | r1 | r2) != 0) {
                     a.okey[obase] = lo;
-                    if (KIND == PM_COEF_M61) {
-                        a.ocoef[obase] = r0;
-                    } else {
-                        a.ocoef[2 * obase] = r0;
-                        a.ocoef[2 * obase + 1] = r1;
-                    }
+                    a.ocoef[OW * obase] = r0;
+                    if (OW > 1) a.ocoef[OW * obase + 1] = r1;
+                    if (OW > 2) a.ocoef[OW * obase + 2] = r2;
                     cnt = 1;
                 }
                 a.ucount[k] = cnt;
@@ -244,28 +248,26 @@ __global__ void __launch_bounds__(RK_THREADS) k_range_sort(RangeArgs a, u32 chun
         u64 run = 0;
         for (u32 c0 = 0; c0 < n; c0 += RK_THREADS) {
             const u32 i = c0 + tid;
-            u64 v0 = 0, v1 = 0;
+            u64 v0 = 0, v1 = 0, v2 = 0;
             bool nz = false;
             if (i < n && (i == 0 || m.kA[i] != m.kA[i - 1])) {
                 const u64 key = m.kA[i];
                 for (u32 jj = i; jj < n && m.kA[jj] == key; jj++) {
                     const u32 src = m.iA[jj];
                     if (KIND == PM_COEF_M61) v0 = m61_add(v0, m.cv[src]);
+                    else if (W3) add192(v0, v1, v2, m.cv[src], m.cv[chunk + src]);
                     else add128(v0, v1, m.cv[src], m.cv[chunk + src]);
                 }
-                nz = (v0 | v1) != 0;
+                nz = (v0 | v1 | v2) != 0;
             }
             u64 cnt;
             u64 pos = block_exclusive_scan(nz ? 1 : 0, cnt, ws);
             if (nz) {
                 const u64 d = obase + run + pos;
                 a.okey[d] = lo + m.kA[i];
-                if (KIND == PM_COEF_M61) {
-                    a.ocoef[d] = v0;
-                } else {
-                    a.ocoef[2 * d] = v0;
-                    a.ocoef[2 * d + 1] = v1;
-                }
+                a.ocoef[OW * d] = v0;
+                if (OW > 1) a.ocoef[OW * d + 1] = v1;
+                if (OW > 2) a.ocoef[OW * d + 2] = v2;
             }
             run += cnt;
         }
@@ -296,9 +298,12 @@ void launch_range_sort(Ctx &c, const RangeArgs &a, u32 chunk, int kind, unsigned
     if (kind == PM_COEF_M61) {
         set_smem(k_range_sort<PM_COEF_M61>, bytes);
         k_range_sort<PM_COEF_M61><<<grid, RK_THREADS, bytes, c.s>>>(a, chunk);
-    } else {
+    } else if (kind == PM_COEF_I64_ACC128) {
         set_smem(k_range_sort<PM_COEF_I64_ACC128>, bytes);
         k_range_sort<PM_COEF_I64_ACC128><<<grid, RK_THREADS, bytes, c.s>>>(a, chunk);
+    } else {
+        set_smem(k_range_sort<PM_COEF_I64_ACC192>, bytes);
+        k_range_sort<PM_COEF_I64_ACC192><<<grid, RK_THREADS, bytes, c.s>>>(a, chunk);
     }
     PM_LAUNCHED(c);
 }

@@ -268,6 +268,47 @@ def test_hash_windows_split_when_full():
     assert_same(gpu, ref, w.field_bits)
 
 
+@pytest.mark.parametrize("strategy", ["direct", "sort", "hash"])
+def test_int192_exact_beyond_int128(strategy):
+    """int64 coefficients up to 2^62 in magnitude with up to ~40 products per
+    result monomial: sums beyond 2^127, which the 128-bit kind refuses
+    (PM_ECOEF_BOUND) and the 192-bit kind computes exactly, compared with
+    the exact-integer oracle."""
+    import paper_1303_7425_gb300 as P
+    st = polygen.Stream(33, 0)
+    mons = polygen.monomials_total_degree(3, 6)                 # 84 monomials
+    fe = np.concatenate([mons, st.below(7, 200 * 3).astype(np.uint32).reshape(200, 3)])
+    ge = np.concatenate([mons[::-1], st.below(7, 150 * 3).astype(np.uint32).reshape(150, 3)])
+    fc = st.coef_i64(len(fe), 2**62)
+    gc = st.coef_i64(len(ge), 2**62)
+    fc[0] = gc[0] = -(2**62)
+    bits = [10, 10, 10]
+    # repeated monomials are summed on load: keep every combined value in int64
+    fe, fc = _combine_in_int64(fe, fc)
+    ge, gc = _combine_in_int64(ge, gc)
+    e, c = oracle.mul_exact(3, bits, fe, fc, ge, gc)
+    vals = [int(x[0]) | (int(x[1]) << 64) | (int(x[2]) << 128) for x in c]
+    assert any(abs(v - (1 << 192) if v >> 191 else v) >= 2**127 for v in vals)
+    with pytest.raises(P.PolymulError) as ei:
+        run_gpu(bits, "i64", fe, fc, ge, gc, strategy=strategy)
+    assert ei.value.code == -3
+    gpu = run_gpu(bits, "i192", fe, fc, ge, gc, strategy=strategy)
+    assert gpu[2]["strategy"] == strategy
+    assert_same(gpu, (e, c), bits)
+
+
+def _combine_in_int64(e, c):
+    """Merge repeated exponent rows, keeping each sum inside int64 by
+    dropping the repeats that would leave it."""
+    seen = {}
+    for row, v in zip(map(tuple, e.tolist()), c.tolist()):
+        s = seen.get(row, 0) + int(v)
+        if -2**63 <= s < 2**63 and s != 0:
+            seen[row] = s
+    rows = list(seen)
+    return np.array(rows, dtype=np.uint32), np.array([seen[r] for r in rows], dtype=np.int64)
+
+
 def test_int128_near_bound():
     a, b = -2**63, 2**63 - 1
     fe = np.array([[0], [1]], np.uint32)

@@ -411,3 +411,72 @@ def test_paper_examples_2_3_operands():
         w = polygen.paper_example(name)
         assert w.f.n == w.g.n == n
     assert math.comb(30, 5) == 142506 and math.comb(33, 5) == 237336
+
+
+# ---------------------------------------------------------------------------
+# the exact-integer product (reference of the 192-bit kind)
+# ---------------------------------------------------------------------------
+
+def _from_words(c3):
+    v = int(c3[0]) | (int(c3[1]) << 64) | (int(c3[2]) << 128)
+    return v - (1 << 192) if v >> 191 else v
+
+
+def test_exact_agrees_with_c_oracle_within_int128():
+    """Two independent implementations (C with int128, Python integers)
+    agree wherever int128 suffices."""
+    st = polygen.Stream(91, 0)
+    for nv, nf, ng in ((2, 40, 30), (3, 120, 90)):
+        fe = st.below(6, nf * nv).astype(np.uint32).reshape(nf, nv)
+        ge = st.below(6, ng * nv).astype(np.uint32).reshape(ng, nv)
+        fc = st.coef_i64(nf, 1 << 40)
+        gc = st.coef_i64(ng, 1 << 40)
+        e1, c1 = oracle.mul(nv, [8] * nv, "i64", fe, fc, ge, gc)
+        e2, c2 = oracle.mul_exact(nv, [8] * nv, fe, fc, ge, gc)
+        np.testing.assert_array_equal(e1, e2)
+        v1 = [int(c[0]) | (int(c[1]) << 64) for c in c1]
+        v1 = [v - (1 << 128) if v >> 127 else v for v in v1]
+        assert v1 == [_from_words(c) for c in c2]
+
+
+def test_exact_closed_form_beyond_int128():
+    """a (1 + x + ... + x^(n-1)) times b (1 + ... + x^(m-1)) with a, b near
+    -2^63 and 2^63: the coefficient of x^k is a b times the number of pairs
+    i + j = k, min(k + 1, n, m, n + m - 1 - k), up to 2^126 * 40 > 2^127."""
+    a, b = -(2**63), 2**63 - 1
+    n, m = 50, 40
+    fe = np.arange(n, dtype=np.uint32).reshape(-1, 1)
+    ge = np.arange(m, dtype=np.uint32).reshape(-1, 1)
+    e, c = oracle.mul_exact(1, [16], fe, np.full(n, a, np.int64), ge, np.full(m, b, np.int64))
+    assert e[:, 0].tolist() == list(range(n + m - 1))
+    for k, ck in zip(e[:, 0].tolist(), c):
+        assert _from_words(ck) == a * b * min(k + 1, n, m, n + m - 1 - k)
+    assert max(abs(_from_words(ck)) for ck in c) > 2**127
+
+
+def test_exact_brute_force_dense_convolution():
+    """Tiny random cases with full-range int64 coefficients against a dense
+    two-variable convolution in Python integers."""
+    st = polygen.Stream(92, 0)
+    for _ in range(3):
+        fe = st.below(4, 10 * 2).astype(np.uint32).reshape(10, 2)
+        ge = st.below(4, 8 * 2).astype(np.uint32).reshape(8, 2)
+        fc = st.coef_i64(10, 2**62)
+        gc = st.coef_i64(8, 2**62)
+        A = [[0] * 4 for _ in range(4)]
+        B = [[0] * 4 for _ in range(4)]
+        for (x, y), v in zip(fe.tolist(), fc.tolist()):
+            A[x][y] += v
+        for (x, y), v in zip(ge.tolist(), gc.tolist()):
+            B[x][y] += v
+        H = {}
+        for i in range(4):
+            for j in range(4):
+                for k in range(4):
+                    for l in range(4):
+                        if A[i][j] and B[k][l]:
+                            H[(i + k, j + l)] = H.get((i + k, j + l), 0) + A[i][j] * B[k][l]
+        want = sorted((k, v) for k, v in H.items() if v)
+        e, c = oracle.mul_exact(2, [8, 8], fe, fc, ge, gc)
+        assert [tuple(x) for x in e.tolist()] == [k for k, _ in want]
+        assert [_from_words(x) for x in c] == [v for _, v in want]
