@@ -66,6 +66,25 @@ def parse_args():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The largest x over all ranks (every rank gets it); x itself without
+    a process group.  device: where the backend reduces ("cuda" for NCCL,
+    "cpu" for gloo)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: int, world: int, slowest_ms: float) -> float:
+    """Units per second of the whole job: every rank processes its own
+    units (replicas, weak scaling), and the job takes as long as the
+    slowest rank."""
+    return world * units_per_rank / (slowest_ms * 1e-3)
+
+
 def env_rank():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
             int(os.environ.get("WORLD_SIZE", "1")))
@@ -519,12 +538,8 @@ def run_ours(args):
     clocks = sampler.stop(t0, t1)
 
     ms = planned[0] if planned else ms_plain
-    ms_step = statistics.mean(ms)
-    if dist:
-        tt = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
-    value = world * products / (ms_step * 1e-3)
+    ms_step = max_over_ranks(statistics.mean(ms), dist, "cuda")
+    value = whole_job_value(products, world, ms_step)
     kern_ms = statistics.mean(s["ms_range_kernel"] for s in stats)
     # kernels per step: the call's launches (+ the plan's two check kernels)
     launches = sum(s["kernel_launches"] + (2 if planned else 0) for s in stats)
@@ -550,7 +565,9 @@ def run_ours(args):
                                     "ms_per_step": statistics.mean(ms_plain),
                                     "host_syncs_per_step": stats[-1]["host_syncs"],
                                     "api": "pm_polymul (host reads sizes between steps)"}}
-        if not args.no_extras:
+        # the secondary workloads run on one GPU only (with N ranks the
+        # others would wait for rank 0 at the closing barrier)
+        if not args.no_extras and world == 1:
             wi = polygen.workload_c2("i64")
             ms_i, st_i, _ = time_product(P, torch, wi, 20, 3, flush, kind="i64")
             extras["c2_int64_acc128"] = {"value": wi.term_products / (statistics.mean(ms_i) * 1e-3), "unit": UNIT,
