@@ -274,8 +274,10 @@ typedef struct pm_batch_item {
 } pm_batch_item;
 
 typedef struct pm_batch_options {
-    uint32_t range_target;     /* term products per output range (64..3072;
-                                  default 2048)                                   */
+    uint32_t range_target;     /* term products per output range: 64..4096 when
+                                  every item is PM_COEF_M61 (default 3072),
+                                  64..3072 otherwise (default 2048); a larger
+                                  value is PM_EINVAL                              */
     uint32_t ranges_per_item;  /* consecutive ranges per work item (default 16)   */
 } pm_batch_options;
 

@@ -35,14 +35,18 @@ constexpr int CAN_IPT = 8;                        // 8192 items
 constexpr int PLAN_T = 1024;                      // B2 threads
 constexpr u32 PLAN_SAMPLES = 8192;
 constexpr int RNG_T = 512;                        // B3 threads
-constexpr u32 RNG_CHUNK = 3072;                   // products sorted per piece
-constexpr int RNG_IPT = RNG_CHUNK / RNG_T;
 constexpr u32 RNG_W = RNG_T / 32;
-constexpr u32 RNG_LANE_MAX = (RNG_CHUNK / RNG_W + 31) / 32;  // products (or pairs) per lane of a piece
 constexpr u32 ROWS_PER_T = BT_MAX_TERMS / RNG_T;  // 16
 constexpr u32 RNG_BS = BT_MAX_TERMS;               // g keys staged in shared memory (larger g: read via L1)
 constexpr int RNG_CTAS = 1;                        // B3 CTAs per SM
-constexpr u32 RNG_TARGET_DEFAULT = 2 * RNG_CHUNK / 3;  // term products per range unless tuned
+// Products sorted per piece.  A product takes 8 + 8 (keys) + 2 + 2
+// (indexes) + 8 per coefficient word bytes of shared memory, so a batch
+// whose products are all mod p (one word) fits 4096, the others 3072.
+__host__ __device__ constexpr u32 rng_chunk(u32 cw) { return cw == 1 ? 4096u : 3072u; }
+// term products per range unless tuned (measured on the 4096-product sparse
+// batch: one-word 126 -> 116 ms at 2048 with the wider chunk, 110.5 ms at
+// 3072, no better above)
+__host__ __device__ constexpr u32 rng_target_default(u32 cw) { return cw == 1 ? 3072u : 2048u; }
 constexpr int FIN_T = 512;
 
 // per-product descriptor (device); fields after `out_` are written by the
@@ -346,43 +350,53 @@ struct RngSmem {
     uint16_t *cur;    // per row: first column not yet consumed
     u64 *kA, *kB;     // sort buffers (raw product keys)
     uint16_t *iA, *iB;
-    u64 *cv;          // product coefficients: lo words [0, CHUNK), hi words [CHUNK, 2 CHUNK)
+    u64 *cv;          // product coefficients: word k of product q at cv[k * CHUNK + q]
     u32 *hist;
 };
 
-// sort histogram; also holds a piece's compacted row tables
-constexpr u32 RNG_HIST_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
-constexpr size_t RNG_SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 + RNG_CHUNK * (8 + 8 + 2 + 2 + 16) +
-                            RNG_HIST_WORDS * 4;
+// Per coefficient word count CW: the chunk, sort items per thread, products
+// per lane of a piece and the shared-memory layout.  The histogram area
+// also holds a piece's compacted row tables: the c-th row with products is
+// crow[c] and its products start at coff[c] (coff[nnz] = O), u16 arrays at
+// offsets 0 and CROW of the area, which the sort reuses once the products
+// are generated.  The scan of the packed per-thread counts (products in the
+// low word, rows with products in the high word) gives each thread's
+// starts; rng_piece's first barrier publishes the tables.
+template <u32 CW>
+struct Rng {
+    static constexpr u32 CHUNK = rng_chunk(CW);
+    static constexpr int IPT = CHUNK / RNG_T;
+    static constexpr u32 LANE_MAX = (CHUNK / RNG_W + 31) / 32;  // products (or pairs) per lane of a piece
+    static constexpr u32 CROW = CHUNK + 8;
+    static constexpr u32 SORT_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
+    static constexpr u32 TABLE_WORDS = ((CROW + CHUNK) * 2 + 15) / 16 * 4;
+    static constexpr u32 HIST_WORDS = SORT_WORDS > TABLE_WORDS ? SORT_WORDS : TABLE_WORDS;
+    static constexpr size_t SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 +
+                                   (size_t)CHUNK * (8 + 8 + 2 + 2 + 8 * CW) + (size_t)HIST_WORDS * 4;
+    static_assert((CROW + CHUNK) * 2 <= HIST_WORDS * 4, "row tables overflow the histogram area");
+    static_assert(CHUNK <= 65535 && CHUNK % RNG_T == 0, "16-bit product offsets, whole sort items per thread");
 
-__device__ __forceinline__ RngSmem carve_rng(unsigned char *p)
-{
-    RngSmem m;
-    m.Bs = (u64 *)p;
-    m.kA = m.Bs + RNG_BS;
-    m.kB = m.kA + RNG_CHUNK;
-    m.cv = m.kB + RNG_CHUNK;
-    m.hist = (u32 *)(m.cv + 2 * RNG_CHUNK);
-    m.cur = (uint16_t *)(m.hist + RNG_HIST_WORDS);
-    m.iA = m.cur + BT_MAX_TERMS;
-    m.iB = m.iA + RNG_CHUNK;
-    return m;
-}
-
-// A piece's rows that have products, compacted: the c-th such row is
-// crow[c] and its products start at coff[c] (coff[nnz] = O).  Both live in
-// the histogram area, which the sort reuses once the products are
-// generated.  The scan of the packed per-thread counts (products in the low
-// word, rows with products in the high word) gives this thread's starts.
-// rng_piece's first barrier publishes the tables.
-constexpr u32 RNG_CROW = RNG_CHUNK + 8;  // u16 offset of crow in the area
-static_assert((RNG_CROW + RNG_CHUNK) * 2 <= RNG_HIST_WORDS * 4, "row tables overflow the histogram area");
+    static __device__ __forceinline__ RngSmem carve(unsigned char *p)
+    {
+        RngSmem m;
+        m.Bs = (u64 *)p;
+        m.kA = m.Bs + RNG_BS;
+        m.kB = m.kA + CHUNK;
+        m.cv = m.kB + CHUNK;
+        m.hist = (u32 *)(m.cv + CW * CHUNK);
+        m.cur = (uint16_t *)(m.hist + HIST_WORDS);
+        m.iA = m.cur + BT_MAX_TERMS;
+        m.iB = m.iA + CHUNK;
+        return m;
+    }
+};
 
 __device__ __forceinline__ u64 row_counts(u32 cnt) { return (u64)cnt | ((u64)(cnt != 0) << 32); }
 
+template <u32 CW>
 __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 r0, u32 r1, const u32 *jh, u64 base, u64 total)
 {
-    uint16_t *coff = (uint16_t *)m.hist, *crow = coff + RNG_CROW;
+    uint16_t *coff = (uint16_t *)m.hist, *crow = coff + Rng<CW>::CROW;
     u32 pb = (u32)base, cb = (u32)(base >> 32);
     for (u32 r = r0; r < r1; r++) {
         const u32 cnt = jh[r - r0] - m.cur[r];
@@ -398,18 +412,21 @@ __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 r0, u32 r1, const 
 
 // One piece [plo, phi) whose column edges are cur (start) and jh (end, per
 // thread's rows), with offsets from piece_offsets: generate its
-// O <= RNG_CHUNK products, sort, reduce, and write the non-zero terms at
+// O <= CHUNK products, sort, reduce, and write the non-zero terms at
 // claim_r + written, claim_r being the range's output base as thread 0
 // holds it.  Returns the terms written.  Ends without a barrier: the
 // caller's next scan separates this piece's reads of the shared buffers
 // from the next piece's writes.
+template <u32 CW>
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                          u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws)
 {
+    typedef Rng<CW> R;
     const u32 tid = threadIdx.x;
-    const int kind = (int)d.kind;
+    // a one-word batch holds mod-p products only
+    const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     const u32 O = (u32)total, nnz = (u32)(total >> 32);
-    const uint16_t *coff = (const uint16_t *)m.hist, *crow = coff + RNG_CROW;
+    const uint16_t *coff = (const uint16_t *)m.hist, *crow = coff + R::CROW;
     __syncthreads();
     // warp w takes a contiguous slice of the products, lanes interleaved so
     // that neighbouring lanes read neighbouring columns.  The warp first
@@ -419,7 +436,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     {
         const u32 per_warp = ((O + RNG_W - 1) / RNG_W + 31u) & ~31u;
         const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, O);
-        u32 rr[RNG_LANE_MAX], jj[RNG_LANE_MAX];
+        u32 rr[R::LANE_MAX], jj[R::LANE_MAX];
         const u32 q0 = p0 + lane;
         if (p0 < p1) {
             // compacted row holding product p0 (last c with coff[c] <= p0),
@@ -438,7 +455,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
             // set one bit each, and a product's row is ca plus the bits at
             // or below its lane
 #pragma unroll
-            for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+            for (u32 t = 0; t < R::LANE_MAX; t++) {
                 const u32 qa = p0 + 32 * t;
                 if (qa < p1) {
                     const u32 c = ca + 1 + lane;
@@ -452,37 +469,37 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
                 }
             }
 #pragma unroll
-            for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+            for (u32 t = 0; t < R::LANE_MAX; t++) {
                 const u32 q = q0 + 32 * t;
                 if (q < p1) {
                     const u32 r2 = rr[t], j = jj[t];
                     m.kA[q] = A[r2] + m.Bs[j];
                     m.iA[q] = (uint16_t)q;
-                    if (kind == PM_COEF_M61) {
+                    if (m61) {
                         m.cv[q] = m61_reduce(m61_mul_lazy(Ac[r2], Bc[j]));
                     } else {
                         u64 lo2, hi2;
                         mul_i64_wide((i64)Ac[r2], (i64)Bc[j], lo2, hi2);
                         m.cv[q] = lo2;
-                        m.cv[RNG_CHUNK + q] = hi2;
+                        m.cv[R::CHUNK + q] = hi2;
                     }
                 }
             }
         }
     }
     __syncthreads();
-    const u32 n = (u32)(O < RNG_CHUNK ? O : RNG_CHUNK);
-    block_sort_interval<RNG_T, RNG_IPT>(m.kA, m.iA, m.kB, m.iB, n, plo, phi - 1 - plo, m.hist, ws);
+    const u32 n = (u32)(O < R::CHUNK ? O : R::CHUNK);
+    block_sort_interval<RNG_T, R::IPT>(m.kA, m.iA, m.kB, m.iB, n, plo, phi - 1 - plo, m.hist, ws);
     // segmented reduction: warp w owns the run heads in a contiguous
     // segment of the sorted pairs (a run may continue past it); positions
     // come from ballots and one block scan over the warps' counts
     const u32 seg = ((n + RNG_W - 1) / RNG_W + 31u) & ~31u;
     const u32 s0 = w * seg, s1 = min(s0 + seg, n);
-    u64 v0[RNG_LANE_MAX], v1[RNG_LANE_MAX];
-    u32 nzmask[RNG_LANE_MAX];
+    u64 v0[R::LANE_MAX], v1[R::LANE_MAX];
+    u32 nzmask[R::LANE_MAX];
     u32 wcount = 0;
 #pragma unroll
-    for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+    for (u32 t = 0; t < R::LANE_MAX; t++) {
         const u32 i = s0 + 32 * t + lane;
         v0[t] = 0;
         v1[t] = 0;
@@ -491,8 +508,8 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
             const u64 key = m.kA[i];
             for (u32 j = i; j < n && m.kA[j] == key; j++) {
                 const u32 src = m.iA[j];
-                if (kind == PM_COEF_M61) v0[t] = m61_add(v0[t], m.cv[src]);
-                else add128(v0[t], v1[t], m.cv[src], m.cv[RNG_CHUNK + src]);
+                if (m61) v0[t] = m61_add(v0[t], m.cv[src]);
+                else add128(v0[t], v1[t], m.cv[src], m.cv[R::CHUNK + src]);
             }
             nz = (v0[t] | v1[t]) != 0;
         }
@@ -509,29 +526,30 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     const u64 out = *s_out;
     u32 before = 0;
 #pragma unroll
-    for (u32 t = 0; t < RNG_LANE_MAX; t++) {
+    for (u32 t = 0; t < R::LANE_MAX; t++) {
         const u32 i = s0 + 32 * t + lane;
         if ((nzmask[t] >> lane) & 1u) {
             const u64 dst = out + wbase + before + (u32)__popc(nzmask[t] & ((1u << lane) - 1u));
             a.skey[dst] = m.kA[i];
-            a.scoef[a.cw * dst] = v0[t];
-            if (a.cw == 2) a.scoef[2 * dst + 1] = v1[t];
+            a.scoef[CW * dst] = v0[t];
+            if (CW == 2) a.scoef[2 * dst + 1] = v1[t];
         }
         before += (u32)__popc(nzmask[t]);
     }
     return nout;
 }
 
-// sum of all products of a single-monomial piece with more than RNG_CHUNK
+// sum of all products of a single-monomial piece with more than CHUNK
 // products; writes at most one term
+template <u32 CW>
 __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                           u32 r0, u32 r1, const u32 *jh, u64 key, u64 out, u64 *ws)
 {
-    const int kind = (int)d.kind;
+    const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     u64 s0 = 0, s1 = 0;
     for (u32 r = r0; r < r1; r++)
         for (u32 j = m.cur[r]; j < jh[r - r0]; j++) {
-            if (kind == PM_COEF_M61) {
+            if (m61) {
                 s0 = m61_add(s0, m61_reduce(m61_mul_lazy(Ac[r], Bc[j])));
             } else {
                 u64 lo, hi;
@@ -545,7 +563,7 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
 #pragma unroll
     for (int dd = 16; dd > 0; dd >>= 1) {
         const u64 o0 = __shfl_down_sync(0xffffffffu, s0, dd), o1 = __shfl_down_sync(0xffffffffu, s1, dd);
-        if (kind == PM_COEF_M61) s0 = m61_add(s0, o0);
+        if (m61) s0 = m61_add(s0, o0);
         else add128(s0, s1, o0, o1);
     }
     if (lane == 0) {
@@ -557,14 +575,14 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
     if (threadIdx.x == 0) {
         u64 r0w = 0, r1w = 0;
         for (int ww = 0; ww < RNG_T / 32; ww++) {
-            if (kind == PM_COEF_M61) r0w = m61_add(r0w, red[2 * ww]);
+            if (m61) r0w = m61_add(r0w, red[2 * ww]);
             else add128(r0w, r1w, red[2 * ww], red[2 * ww + 1]);
         }
         wrote = 0;
         if ((r0w | r1w) != 0) {
             a.skey[out] = key;
-            a.scoef[a.cw * out] = r0w;
-            if (a.cw == 2) a.scoef[2 * out + 1] = r1w;
+            a.scoef[CW * out] = r0w;
+            if (CW == 2) a.scoef[2 * out + 1] = r1w;
             wrote = 1;
         }
     }
@@ -572,13 +590,15 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
     return wrote;
 }
 
+template <u32 CW>
 __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
 {
+    typedef Rng<CW> R;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
     __shared__ u32 item;
     __shared__ u64 claim;
-    RngSmem m = carve_rng(smem);
+    RngSmem m = R::carve(smem);
     const u32 tid = threadIdx.x;
     for (;;) {
         if (tid == 0) item = atomicAdd(a.work, 1u);
@@ -652,16 +672,16 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             u64 claim_r = 0;
             if (tid == 0) claim_r = atomicAdd(a.bump, O);
             u64 written = 0;
-            if (O <= RNG_CHUNK) {
+            if (O <= R::CHUNK) {
                 if (O) {
-                    piece_offsets(m, r0, r1, jh, base, tot);
-                    written = rng_piece(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
+                    piece_offsets<CW>(m, r0, r1, jh, base, tot);
+                    written = rng_piece<CW>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
                 }
                 // own rows only: other threads read these cursors after the
                 // next scan
                 for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
             } else {
-                // bisect by key: pieces [plo, phi) with at most RNG_CHUNK
+                // bisect by key: pieces [plo, phi) with at most CHUNK
                 // products, or a single monomial
                 u64 plo = rlo_k;
                 while (plo < rhi_k) {
@@ -677,15 +697,15 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                         u64 ptot;
                         const u64 pbase = block_exclusive_scan(cnt_mine, ptot, ws);
                         const u64 PO = (u32)ptot;
-                        if (PO <= RNG_CHUNK) {
+                        if (PO <= R::CHUNK) {
                             if (PO) {
-                                piece_offsets(m, r0, r1, jh, pbase, ptot);
-                                written += rng_piece(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
+                                piece_offsets<CW>(m, r0, r1, jh, pbase, ptot);
+                                written += rng_piece<CW>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
                             }
                             break;
                         }
                         if (phi - plo == 1) {
-                            written += rng_single(a, d, m, A, Ac, Bc, r0, r1, jh, plo, claim_r + written, ws);
+                            written += rng_single<CW>(a, d, m, A, Ac, Bc, r0, r1, jh, plo, claim_r + written, ws);
                             break;
                         }
                         phi = plo + (phi - plo) / 2;
@@ -834,9 +854,12 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
     BatchSizes z;
-    z.target = o.range_target ? o.range_target : RNG_TARGET_DEFAULT;
+    // the coefficient words, hence the chunk and the default target
+    for (u32 p = 0; p < count; p++)
+        if (items[p].coef_kind == PM_COEF_I64_ACC128) z.cw = 2;
+    z.target = o.range_target ? o.range_target : rng_target_default(z.cw);
     z.per_item = o.ranges_per_item ? o.ranges_per_item : 16;
-    if (z.target < 64 || z.target > RNG_CHUNK || z.per_item < 1 || z.per_item > 4096)
+    if (z.target < 64 || z.target > rng_chunk(z.cw) || z.per_item < 1 || z.per_item > 4096)
         throw Error(PM_EINVAL, "bad batch options");
     for (u32 p = 0; p < count; p++) {
         const pm_batch_item &it = items[p];
@@ -859,7 +882,6 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
         }
         if (sbits > 64) throw Error(PM_EINVAL, "fields exceed 64 bits");
         d.kind = it.coef_kind;
-        if (it.coef_kind == PM_COEF_I64_ACC128) z.cw = 2;
         d.fe = it.f.exps;
         d.fc = (const u64 *)it.f.coefs;
         d.nf = (u32)it.f.n;
@@ -921,7 +943,8 @@ static void set_batch_smem()
 {
     set_smem_b(kb_canon, CAN_SMEM);
     set_smem_b(kb_plan, PLAN_SMEM);
-    set_smem_b(kb_ranges, RNG_SMEM);
+    set_smem_b(kb_ranges<1>, Rng<1>::SMEM);
+    set_smem_b(kb_ranges<2>, Rng<2>::SMEM);
 }
 
 // the four kernels of the pass (counters cleared first)
@@ -933,7 +956,10 @@ static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
     PM_CUDA(cudaGetLastError());
     kb_plan<<<a.count, PLAN_T, PLAN_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
-    kb_ranges<<<sm_count * RNG_CTAS, RNG_T, RNG_SMEM, s>>>(a);
+    if (a.cw == 1)
+        kb_ranges<1><<<sm_count * RNG_CTAS, RNG_T, Rng<1>::SMEM, s>>>(a);
+    else
+        kb_ranges<2><<<sm_count * RNG_CTAS, RNG_T, Rng<2>::SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
     kb_finish<<<a.count, FIN_T, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());
@@ -1098,7 +1124,7 @@ int batch_collect_ws(pm_batch_item *items, u32 count, const void *hws)
 
 void batch_prepare_device() { set_batch_smem(); }
 
-u32 batch_range_chunk() { return RNG_CHUNK; }
+u32 batch_range_chunk(u32 cw) { return rng_chunk(cw); }
 
 }  // namespace pm
 

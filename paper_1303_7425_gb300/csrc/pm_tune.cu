@@ -50,7 +50,7 @@ ShapeKey shape_key(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box)
 }
 
 // used by pm_polymul when its options are all defaults
-u32 batch_range_chunk();  // pm_batch.cu
+u32 batch_range_chunk(u32 cw);  // pm_batch.cu
 
 bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box, pm_options &o)
 {
@@ -176,9 +176,14 @@ extern "C" int pm_batch_autotune(const pm_batch_item *items, uint32_t count, pm_
     float best_ms = 1e30f;
     int best_k = -1;
     int k = 0;
-    // range sizes: fractions of the range kernel's shared-memory chunk
-    const u32 ch = batch_range_chunk();
-    for (uint32_t target : {ch / 3, ch / 2, 2 * ch / 3, ch}) {
+    // range sizes: fractions of the range kernel's shared-memory chunk,
+    // which depends on the coefficient words of the whole batch (the
+    // winner must be valid for every item, sampled or not)
+    u32 cw = 1;
+    for (uint32_t q = 0; q < count; q++)
+        if (items[q].coef_kind == PM_COEF_I64_ACC128) cw = 2;
+    const u32 ch = batch_range_chunk(cw);
+    for (uint32_t target : {ch / 3, ch / 2, 3 * ch / 4, ch}) {
         for (uint32_t per : {8u, 16u, 64u}) {
             pm_batch_options o = {target, per};
             pm_batch_plan *pl = nullptr;

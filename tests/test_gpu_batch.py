@@ -71,6 +71,35 @@ def test_batch_matches_oracle_and_single(opts):
         np.testing.assert_array_equal(single.coefs.cpu().numpy(), pr["out"][1][:n].cpu().numpy())
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(range_target=4096, ranges_per_item=64),
+                                  dict(range_target=100, ranges_per_item=3)])
+def test_batch_mod_p_only_wider_chunk(opts):
+    """A batch whose products are all mod p keeps one coefficient word per
+    product in shared memory and sorts up to 4096 products per piece; ranges
+    up to that size (and the bisection above it) stay exact."""
+    import paper_1303_7425_gb300 as P
+    ws = [w for w in _mixed_workloads(seed=17, count=24) if w.kind == "m61"]
+    prods = [_product(w) for w in ws]
+    res, stats = P.batch_polymul(prods, **opts)
+    assert stats["graph"] == 1
+    for pr, (status, n) in zip(prods, res):
+        assert status == 0
+        _check_against_oracle(pr, n)
+
+
+def test_batch_range_target_limit_depends_on_kinds():
+    """4096 products per range fit only one coefficient word per product: with
+    an int64 item in the batch the same option is rejected."""
+    import paper_1303_7425_gb300 as P
+    ws = _mixed_workloads(seed=19, count=3)
+    assert any(w.kind == "i64" for w in ws)
+    with pytest.raises(P.PolymulError) as ei:
+        P.batch_polymul([_product(w) for w in ws], range_target=4096)
+    assert ei.value.code == -1
+    res, _ = P.batch_polymul([_product(w) for w in ws], range_target=3072)
+    assert all(st == 0 for st, _ in res)
+
+
 def test_batch_errors_stay_per_item():
     import paper_1303_7425_gb300 as P
     ws = _mixed_workloads(count=6)
