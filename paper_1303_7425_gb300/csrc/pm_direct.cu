@@ -592,68 +592,145 @@ __global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__rest
 // default, the autotuner picks the weights per shape class).  K_b = cost_row rows + cost_window is
 // a window's cost near bucket b; a bucket of bw ranks carries bw / win of
 // it (kw keeps K_b for the refinement below).
-__global__ void k_hist_rows(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, u64 lo, u64 bw,
-                            u64 win, u64 nbk, u64 cost_row, u64 cost_window, u64 *__restrict__ hist,
-                            u64 *__restrict__ kw)
+// (Both histogram kernels run HB-thread blocks, one bucket per thread, and
+// leave the sum of each block's final bucket values in part[block] for
+// k_group_cut.)
+constexpr int HB = 256;
+
+// sum over the block of one value per thread, in thread 0; all threads call
+__device__ __forceinline__ u64 block_sum_u64(u64 v, u64 *ws)
 {
-    const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nbk) return;
-    const u64 bmin = B[0], bmax = B[nb - 1];
-    const u64 x0 = lo + k * bw, x1 = x0 + win;
-    const u32 i_lo = x0 > bmax ? lower_bound_u64(A, na, x0 - bmax) : 0u;
-    const u32 i_hi = x1 > bmin ? lower_bound_u64(A, na, x1 - bmin) : 0u;
-    const u64 rows = i_hi > i_lo ? i_hi - i_lo : 0;
-    const u64 K = cost_row * rows + cost_window;
-    kw[k] = K;
-    hist[k] += (u64)(((unsigned __int128)K * bw) / win) + 1;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_down_sync(0xffffffffu, v, d);
+    const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) ws[w] = v;
+    __syncthreads();
+    u64 s = 0;
+    if (threadIdx.x == 0)
+        for (u32 q = 0; q < (blockDim.x >> 5); q++) s += ws[q];
+    return s;
+}
+
+__global__ void __launch_bounds__(HB) k_hist_rows(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B,
+                                                  u32 nb, u64 lo, u64 bw, u64 win, u64 nbk, u64 cost_row,
+                                                  u64 cost_window, u64 *__restrict__ hist, u64 *__restrict__ kw,
+                                                  u64 *__restrict__ part)
+{
+    __shared__ u64 ws[32];
+    const u64 k = (u64)blockIdx.x * HB + threadIdx.x;
+    u64 h = 0;
+    if (k < nbk) {
+        const u64 bmin = B[0], bmax = B[nb - 1];
+        const u64 x0 = lo + k * bw, x1 = x0 + win;
+        const u32 i_lo = x0 > bmax ? lower_bound_u64(A, na, x0 - bmax) : 0u;
+        const u32 i_hi = x1 > bmin ? lower_bound_u64(A, na, x1 - bmin) : 0u;
+        const u64 rows = i_hi > i_lo ? i_hi - i_lo : 0;
+        const u64 K = cost_row * rows + cost_window;
+        kw[k] = K;
+        h = hist[k] + (u64)(((unsigned __int128)K * bw) / win) + 1;
+        hist[k] = h;
+    }
+    const u64 t = block_sum_u64(h, ws);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
 // A group narrower than a window still pays one whole window, which the
 // per-bucket share above charged only span / win of: its buckets get the
 // rest, K_b bw (1 / span - 1 / win), before the groups are cut again.
-__global__ void k_hist_narrow(const u64 *__restrict__ gb, u32 G, u64 lo, u64 bw, u64 win, u64 nbk,
-                              const u64 *__restrict__ kw, u64 *__restrict__ hist)
+__global__ void __launch_bounds__(HB) k_hist_narrow(const u64 *__restrict__ gb, u32 G, u64 lo, u64 bw, u64 win,
+                                                    u64 nbk, const u64 *__restrict__ kw, u64 *__restrict__ hist,
+                                                    u64 *__restrict__ part)
 {
-    const u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nbk) return;
-    const u64 x0 = lo + k * bw;
-    // the group holding x0: last g with gb[g] <= x0
-    u32 a = 0, n = G;
-    while (n > 1) {
-        const u32 h = n >> 1;
-        if (gb[a + h] <= x0) {
-            a += h;
-            n -= h;
-        } else {
-            n = h;
+    __shared__ u64 ws[32];
+    const u64 k = (u64)blockIdx.x * HB + threadIdx.x;
+    u64 h = 0;
+    if (k < nbk) {
+        h = hist[k];
+        const u64 x0 = lo + k * bw;
+        // the group holding x0: last g with gb[g] <= x0
+        u32 a = 0, n = G;
+        while (n > 1) {
+            const u32 hh = n >> 1;
+            if (gb[a + hh] <= x0) {
+                a += hh;
+                n -= hh;
+            } else {
+                n = hh;
+            }
+        }
+        const u64 span = gb[a + 1] - gb[a];
+        if (span != 0 && span < win) {
+            h += (u64)(((unsigned __int128)kw[k] * bw * (win - span)) / ((unsigned __int128)span * win));
+            hist[k] = h;
         }
     }
-    const u64 span = gb[a + 1] - gb[a];
-    if (span == 0 || span >= win) return;
-    const unsigned __int128 add = ((unsigned __int128)kw[k] * bw * (win - span)) / ((unsigned __int128)span * win);
-    hist[k] += (u64)add;
+    const u64 t = block_sum_u64(h, ws);
+    if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// group m starts at the first bucket whose cumulative cost reaches m W / G
-__global__ void k_group_bounds(const u64 *__restrict__ cw, u64 nbk, u32 G, u64 lo, u64 end, u64 bw,
-                               u64 *__restrict__ gb)
+// Group boundaries from the bucket costs: with c_i the cost of the buckets
+// below i (c_0 = 0, c_nbk = W), group m (0 < m < G) starts at bucket
+// i(m) = the first i with c_i >= floor(W m / G), i.e. at lo + i(m) bw (at
+// most end); gb[0] = lo and gb[G] = end.  One pass: each block takes GC_PER
+// consecutive buckets per thread, finds the cost below its first bucket
+// from the histogram kernels' per-block sums, scans its own buckets, and
+// the bucket i - 1 whose interval (c_{i-1}, c_i] holds floor(W m / G)
+// writes gb[m].
+constexpr int GC_T = 1024, GC_PER = 4;
+constexpr u32 GC_BUCKETS = GC_T * GC_PER;
+static_assert(GC_BUCKETS % HB == 0, "whole histogram blocks per cut block");
+
+__device__ __forceinline__ void cut_emit(u64 a, u64 b, u64 i, u64 W, u32 G, u64 lo, u64 end, u64 bw,
+                                         u64 *__restrict__ gb)
 {
-    u32 m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m > G) return;
-    u64 v;
-    if (m == 0) {
-        v = lo;
-    } else if (m == G) {
-        v = end;
-    } else {
-        const u64 W = cw[nbk];
-        const u64 target = (u64)(((unsigned __int128)W * m) / G);
-        u64 k = lower_bound_u64(cw, (u32)(nbk + 1), target);
-        if (k > nbk) k = nbk;
-        v = lo + k * bw;
-        if (v > end) v = end;
+    // m with a < floor(W m / G) <= b: from ceil((a + 1) G / W) while in range
+    u64 m = (u64)(((unsigned __int128)(a + 1) * G + W - 1) / W);
+    u64 v = lo + i * bw;
+    if (v > end) v = end;
+    for (; m < G; m++) {
+        if ((u64)(((unsigned __int128)W * m) / G) > b) break;
+        gb[m] = v;
     }
-    gb[m] = v;
+}
+
+__global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist, const u64 *__restrict__ part,
+                                                    u32 nparts, u64 nbk, u32 G, u64 lo, u64 end, u64 bw,
+                                                    u64 *__restrict__ gb)
+{
+    __shared__ u64 ws[32];
+    const u32 tid = threadIdx.x;
+    const u32 pb = blockIdx.x * (GC_BUCKETS / HB);  // histogram blocks before this block's buckets
+    u64 below = 0, all = 0;
+    for (u32 q = tid; q < nparts; q += GC_T) {
+        const u64 v = part[q];
+        all += v;
+        if (q < pb) below += v;
+    }
+    u64 W, base;
+    block_exclusive_scan(all, W, ws);
+    block_exclusive_scan(below, base, ws);
+    const u64 k0 = (u64)blockIdx.x * GC_BUCKETS + (u64)tid * GC_PER;
+    u64 h[GC_PER];
+    u64 mine = 0;
+#pragma unroll
+    for (int t = 0; t < GC_PER; t++) {
+        h[t] = k0 + t < nbk ? hist[k0 + t] : 0;
+        mine += h[t];
+    }
+    u64 tot;
+    u64 c = base + block_exclusive_scan(mine, tot, ws);  // c_{k0}
+    if (W == 0) return;
+#pragma unroll
+    for (int t = 0; t < GC_PER; t++) {
+        if (k0 + t < nbk) cut_emit(c, c + h[t], k0 + t + 1, W, G, lo, end, bw, gb);
+        c += h[t];
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        gb[0] = lo;
+        gb[G] = end;
+        // floor(W m / G) <= c_0 = 0: i(m) = 0
+        for (u64 m = 1; m < G && (u64)(((unsigned __int128)W * m) / G) == 0; m++) gb[m] = lo;
+    }
 }
 
 u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u64 lo, u64 end, u32 G,
@@ -670,7 +747,8 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     const u64 span = end - lo;
     const u64 nbk = span < nbk_max ? span : nbk_max;
     const u64 bw = (span + nbk - 1) / nbk;
-    u64 *hist = S.get<u64>(nbk), *cw = S.get<u64>(nbk + 1);
+    const u32 nparts = (u32)((nbk + HB - 1) / HB);
+    u64 *hist = S.get<u64>(nbk), *part = S.get<u64>(nparts);
     PM_CUDA(cudaMemsetAsync(hist, 0, nbk * 8, c.s));
     const u64 wg = products / ng + 1;
     k_grid_hist<<<(unsigned)((ng + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, ng, lo, bw, nbk,
@@ -678,18 +756,16 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     PM_LAUNCHED(c);
     u64 *kw = S.get<u64>(nbk);
     const u64 w = win ? win : 1;
-    k_hist_rows<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, lo, bw, w, nbk, cost_row, cost_window,
-                                                                hist, kw);
+    k_hist_rows<<<nparts, HB, 0, c.s>>>(A, na, B, nb, lo, bw, w, nbk, cost_row, cost_window, hist, kw, part);
     PM_LAUNCHED(c);
-    scan_exclusive_u64(c, S, hist, cw, nbk);
     u64 *gb = S.get<u64>(G + 1);
-    k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cw, nbk, G, lo, end, bw, gb);
+    const u32 ncut = (u32)((nbk + GC_BUCKETS - 1) / GC_BUCKETS);
+    k_group_cut<<<ncut, GC_T, 0, c.s>>>(hist, part, nparts, nbk, G, lo, end, bw, gb);
     PM_LAUNCHED(c);
     // one refinement: charge narrow groups their whole window, cut again
-    k_hist_narrow<<<(unsigned)((nbk + 255) / 256), 256, 0, c.s>>>(gb, G, lo, bw, w, nbk, kw, hist);
+    k_hist_narrow<<<nparts, HB, 0, c.s>>>(gb, G, lo, bw, w, nbk, kw, hist, part);
     PM_LAUNCHED(c);
-    scan_exclusive_u64(c, S, hist, cw, nbk);
-    k_group_bounds<<<(G + 256) / 256, 256, 0, c.s>>>(cw, nbk, G, lo, end, bw, gb);
+    k_group_cut<<<ncut, GC_T, 0, c.s>>>(hist, part, nparts, nbk, G, lo, end, bw, gb);
     PM_LAUNCHED(c);
     return gb;
 }
