@@ -36,7 +36,6 @@ constexpr int PLAN_T = 1024;                      // B2 threads
 constexpr u32 PLAN_SAMPLES = 8192;
 constexpr int RNG_T = 512;                        // B3 threads
 constexpr u32 RNG_W = RNG_T / 32;
-constexpr u32 ROWS_PER_T = BT_MAX_TERMS / RNG_T;  // 16
 constexpr u32 RNG_BS = BT_MAX_TERMS;               // g keys staged in shared memory (larger g: read via L1)
 constexpr int RNG_CTAS = 1;                        // B3 CTAs per SM
 // Products sorted per piece.  A product takes 8 + 8 (keys) + 2 + 2
@@ -348,32 +347,31 @@ __device__ __forceinline__ u32 gallop_up(const u64 *B, u32 n, u32 j, u64 x)
 struct RngSmem {
     u64 *Bs;          // g's canonical keys
     uint16_t *cur;    // per row: first column not yet consumed
+    uint16_t *ce;     // per row: the column edge at the current piece's end
     u64 *kA, *kB;     // sort buffers (raw product keys)
     uint16_t *iA, *iB;
     u64 *cv;          // product coefficients: word k of product q at cv[k * CHUNK + q]
-    u32 *hist;
+    u32 *hist;        // bucket counts / offsets of the sort
 };
 
 // Per coefficient word count CW: the chunk, sort items per thread, products
-// per lane of a piece and the shared-memory layout.  The histogram area
-// also holds a piece's compacted row tables: the c-th row with products is
-// crow[c] and its products start at coff[c] (coff[nnz] = O), u16 arrays at
-// offsets 0 and CROW of the area, which the sort reuses once the products
-// are generated.  The scan of the packed per-thread counts (products in the
-// low word, rows with products in the high word) gives each thread's
-// starts; rng_piece's first barrier publishes the tables.
+// per lane of a piece and the shared-memory layout.  While a piece's
+// products are generated, the sort's second key buffer (kB, free until the
+// scatter) holds the piece's compacted row tables: the c-th row with
+// products is crow[c] and its products start at coff[c] (coff[nnz] = O),
+// u16 arrays at offsets 0 and CROW.  The scan of the packed per-thread
+// counts (products in the low word, rows with products in the high word)
+// gives each thread's starts; rng_piece's first barrier publishes them.
 template <u32 CW>
 struct Rng {
     static constexpr u32 CHUNK = rng_chunk(CW);
     static constexpr int IPT = CHUNK / RNG_T;
-    static constexpr u32 LANE_MAX = (CHUNK / RNG_W + 31) / 32;  // products (or pairs) per lane of a piece
+    static constexpr u32 LANE_MAX = (CHUNK / RNG_W + 31) / 32;  // products per lane of a piece
     static constexpr u32 CROW = CHUNK + 8;
-    static constexpr u32 SORT_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
-    static constexpr u32 TABLE_WORDS = ((CROW + CHUNK) * 2 + 15) / 16 * 4;
-    static constexpr u32 HIST_WORDS = SORT_WORDS > TABLE_WORDS ? SORT_WORDS : TABLE_WORDS;
-    static constexpr size_t SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 +
+    static constexpr u32 HIST_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
+    static constexpr size_t SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 * 2 +
                                    (size_t)CHUNK * (8 + 8 + 2 + 2 + 8 * CW) + (size_t)HIST_WORDS * 4;
-    static_assert((CROW + CHUNK) * 2 <= HIST_WORDS * 4, "row tables overflow the histogram area");
+    static_assert((CROW + CHUNK) * 2 <= CHUNK * 8, "row tables overflow the second key buffer");
     static_assert(CHUNK <= 65535 && CHUNK % RNG_T == 0, "16-bit product offsets, whole sort items per thread");
 
     static __device__ __forceinline__ RngSmem carve(unsigned char *p)
@@ -387,19 +385,23 @@ struct Rng {
         m.cur = (uint16_t *)(m.hist + HIST_WORDS);
         m.iA = m.cur + BT_MAX_TERMS;
         m.iB = m.iA + CHUNK;
+        m.ce = m.iB + CHUNK;
         return m;
     }
 };
 
 __device__ __forceinline__ u64 row_counts(u32 cnt) { return (u64)cnt | ((u64)(cnt != 0) << 32); }
 
+// The piece's row tables (in kB), and the sort's bucket counts cleared for
+// the generation to fill.  Runs between the caller's scan and rng_piece's
+// first barrier; the previous piece no longer reads kB or hist by then.
 template <u32 CW>
-__device__ __forceinline__ void piece_offsets(RngSmem &m, u32 r0, u32 r1, const u32 *jh, u64 base, u64 total)
+__device__ __forceinline__ void piece_offsets(RngSmem &m, u32 cf, u64 base, u64 total)
 {
-    uint16_t *coff = (uint16_t *)m.hist, *crow = coff + Rng<CW>::CROW;
+    uint16_t *coff = (uint16_t *)m.kB, *crow = coff + Rng<CW>::CROW;
     u32 pb = (u32)base, cb = (u32)(base >> 32);
-    for (u32 r = r0; r < r1; r++) {
-        const u32 cnt = jh[r - r0] - m.cur[r];
+    for (u32 r = threadIdx.x; r < cf; r += RNG_T) {
+        const u32 cnt = (u32)m.ce[r] - m.cur[r];
         if (cnt) {
             coff[cb] = (uint16_t)pb;
             crow[cb] = (uint16_t)r;
@@ -408,15 +410,112 @@ __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 r0, u32 r1, const 
         }
     }
     if (threadIdx.x == 0) coff[total >> 32] = (uint16_t)total;
+    for (u32 x = threadIdx.x; x < BUCKETS; x += RNG_T) m.hist[x] = 0;
 }
 
-// One piece [plo, phi) whose column edges are cur (start) and jh (end, per
-// thread's rows), with offsets from piece_offsets: generate its
-// O <= CHUNK products, sort, reduce, and write the non-zero terms at
-// claim_r + written, claim_r being the range's output base as thread 0
-// holds it.  Returns the terms written.  Ends without a barrier: the
-// caller's next scan separates this piece's reads of the shared buffers
-// from the next piece's writes.
+// Sorts the piece's n (key, index) pairs in kA/iA by key, the bucket counts
+// having been taken while the products were generated (bucket = the top 12
+// significant bits of key - lo, clamped; with shift 0 one key value per
+// bucket).  Each pair moves once by bucket and once to its place inside the
+// bucket, found by counting the bucket's smaller keys (ties by position);
+// with shift 0 the scatter alone sorts.  Equal keys come out adjacent in no
+// particular order.  A bucket with more than BUCKET_RANK_MAX pairs sends the
+// piece to the LSD radix sort instead.  On return m.kA/m.iA hold the sorted
+// pairs (the buffers may have swapped).  All threads call; ends with a
+// barrier.
+template <u32 CW>
+__device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *ws)
+{
+    typedef Rng<CW> R;
+    constexpr u32 PER = BUCKETS / RNG_T;
+    static_assert(BUCKETS % RNG_T == 0, "buckets per thread");
+    __shared__ u32 s_bmax;
+    const u32 tid = threadIdx.x;
+    if (tid == 0) s_bmax = 0;
+    // exclusive bucket offsets (thread t owns buckets [t PER, t PER + PER))
+    u32 c[PER];
+    u32 sum = 0, mx = 0;
+#pragma unroll
+    for (u32 q = 0; q < PER; q++) {
+        c[q] = m.hist[tid * PER + q];
+        sum += c[q];
+        mx = c[q] > mx ? c[q] : mx;
+    }
+    u64 tot;
+    u32 run = (u32)block_exclusive_scan(sum, tot, ws);  // its barriers order s_bmax = 0 first
+    if (shift > 0 && mx > BUCKET_RANK_MAX) atomicMax(&s_bmax, mx);
+#pragma unroll
+    for (u32 q = 0; q < PER; q++) {
+        m.hist[tid * PER + q] = run;
+        run += c[q];
+    }
+    __syncthreads();
+    if (s_bmax > BUCKET_RANK_MAX) {
+        block_sort_pairs<RNG_T, R::IPT>(m.kA, m.iA, m.kB, m.iB, n, varying_bits(lo, lo + span), m.hist, ws);
+        return;
+    }
+    // scatter by bucket; afterwards hist[b] is the end of bucket b
+    if (shift > 0) {
+        for (u32 q = tid; q < n; q += RNG_T) {
+            const u64 key = m.kA[q];
+            const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
+            const u32 p = atomicAdd(&m.hist[b], 1u);
+            m.kB[p] = key;
+            m.iB[p] = m.iA[q];
+        }
+    } else {
+        // one key value per bucket, often repeated: one atomic per distinct
+        // bucket of a warp
+        const u32 lane = tid & 31, nround = (n + 31u) & ~31u;
+        for (u32 i = tid & ~31u; i < nround; i += RNG_T) {
+            const u32 q = i + lane;
+            const bool valid = q < n;
+            const u64 key = valid ? m.kA[q] : 0;
+            const u32 b = valid ? (u32)min(key - lo, (u64)BUCKETS - 1) : BUCKETS;
+            const u32 peers = __match_any_sync(0xffffffffu, b);
+            const u32 leader = (u32)(__ffs(peers) - 1);
+            u32 base = 0;
+            if (valid && lane == leader) base = atomicAdd(&m.hist[b], (u32)__popc(peers));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (valid) {
+                const u32 p = base + (u32)__popc(peers & ((1u << lane) - 1u));
+                m.kB[p] = key;
+                m.iB[p] = m.iA[q];
+            }
+        }
+    }
+    __syncthreads();
+    if (shift == 0) {
+        u64 *tk = m.kA;
+        m.kA = m.kB;
+        m.kB = tk;
+        uint16_t *ti = m.iA;
+        m.iA = m.iB;
+        m.iB = ti;
+        return;
+    }
+    // rank inside the bucket, written back to the A buffers
+    for (u32 x = tid; x < n; x += RNG_T) {
+        const u64 key = m.kB[x];
+        const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
+        const u32 beg = b ? m.hist[b - 1] : 0u, end = m.hist[b];
+        u32 rank = 0;
+        for (u32 y = beg; y < end; y++) {
+            const u64 o = m.kB[y];
+            rank += (o < key || (o == key && y < x)) ? 1u : 0u;
+        }
+        m.kA[beg + rank] = key;
+        m.iA[beg + rank] = m.iB[x];
+    }
+    __syncthreads();
+}
+
+// One piece [plo, phi) whose column edges are cur (start) and ce (end),
+// with tables from piece_offsets: generate its O <= CHUNK products, sort,
+// reduce, and write the non-zero terms at claim_r + written,
+// claim_r being the range's output base as thread 0 holds it.  Returns the
+// terms written.  Ends without a barrier: the caller's next scan separates
+// this piece's reads of the shared buffers from the next piece's writes.
 template <u32 CW>
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                          u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws)
@@ -426,7 +525,10 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     // a one-word batch holds mod-p products only
     const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     const u32 O = (u32)total, nnz = (u32)(total >> 32);
-    const uint16_t *coff = (const uint16_t *)m.hist, *crow = coff + R::CROW;
+    const uint16_t *coff = (const uint16_t *)m.kB, *crow = coff + R::CROW;
+    // bucket of a key: the top 12 significant bits of key - plo
+    const u64 span = phi - 1 - plo;
+    const int shift = span >> 12 ? 52 - __clzll((long long)span) : 0;
     __syncthreads();
     // warp w takes a contiguous slice of the products, lanes interleaved so
     // that neighbouring lanes read neighbouring columns.  The warp first
@@ -473,8 +575,10 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
                 const u32 q = q0 + 32 * t;
                 if (q < p1) {
                     const u32 r2 = rr[t], j = jj[t];
-                    m.kA[q] = A[r2] + m.Bs[j];
+                    const u64 key = A[r2] + m.Bs[j];
+                    m.kA[q] = key;
                     m.iA[q] = (uint16_t)q;
+                    atomicAdd(&m.hist[(u32)min((key - plo) >> shift, (u64)BUCKETS - 1)], 1u);
                     if (m61) {
                         m.cv[q] = m61_reduce(m61_mul_lazy(Ac[r2], Bc[j]));
                     } else {
@@ -488,8 +592,8 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
         }
     }
     __syncthreads();
-    const u32 n = (u32)(O < R::CHUNK ? O : R::CHUNK);
-    block_sort_interval<RNG_T, R::IPT>(m.kA, m.iA, m.kB, m.iB, n, plo, phi - 1 - plo, m.hist, ws);
+    const u32 n = O;
+    sort_piece<CW>(m, n, plo, span, shift, ws);
     // segmented reduction: warp w owns the run heads in a contiguous
     // segment of the sorted pairs (a run may continue past it); positions
     // come from ballots and one block scan over the warps' counts
@@ -543,12 +647,12 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
 // products; writes at most one term
 template <u32 CW>
 __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
-                          u32 r0, u32 r1, const u32 *jh, u64 key, u64 out, u64 *ws)
+                          u32 cf, u64 key, u64 out, u64 *ws)
 {
     const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     u64 s0 = 0, s1 = 0;
-    for (u32 r = r0; r < r1; r++)
-        for (u32 j = m.cur[r]; j < jh[r - r0]; j++) {
+    for (u32 r = threadIdx.x; r < cf; r += RNG_T)
+        for (u32 j = m.cur[r]; j < m.ce[r]; j++) {
             if (m61) {
                 s0 = m61_add(s0, m61_reduce(m61_mul_lazy(Ac[r], Bc[j])));
             } else {
@@ -626,14 +730,14 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             m.Bs = const_cast<u64 *>(Bg);
         }
         __syncthreads();
-        // rows of this thread: [r0, r1), ceil(cf / RNG_T) <= ROWS_PER_T of
-        // them, so every thread has work; cursors at the first range's start
-        const u32 rpt = (cf + RNG_T - 1) / RNG_T;
-        const u32 r0 = min(tid * rpt, cf), r1 = min(r0 + rpt, cf);
-        u32 jh[ROWS_PER_T];
+        // rows of this thread: tid, tid + RNG_T, ... (neighbouring lanes on
+        // neighbouring rows: coalesced row loads, conflict-free cursors); a
+        // piece's compacted row table lists them thread by thread, which the
+        // generation and the sort do not mind.  Cursors at the first range's
+        // start.
         {
             const u64 lo = a.rlo[d.rg_off + first];
-            for (u32 r = r0; r < r1; r++) {
+            for (u32 r = tid; r < cf; r += RNG_T) {
                 const u64 ar = A[r];
                 u32 c = 0;
                 if (lo > ar) {
@@ -658,10 +762,10 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             const u64 rlo_k = a.rlo[d.rg_off + k], rhi_k = a.rhi[d.rg_off + k];
             // edges at the range end and the range's product count
             u64 mine = 0;
-            for (u32 r = r0; r < r1; r++) {
+            for (u32 r = tid; r < cf; r += RNG_T) {
                 const u64 ar = A[r];
                 const u32 e = rhi_k > ar ? gallop_up(m.Bs, cg, m.cur[r], rhi_k - ar) : m.cur[r];
-                jh[r - r0] = e;
+                m.ce[r] = (uint16_t)e;
                 mine += row_counts(e - m.cur[r]);
             }
             u64 tot;
@@ -674,12 +778,12 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             u64 written = 0;
             if (O <= R::CHUNK) {
                 if (O) {
-                    piece_offsets<CW>(m, r0, r1, jh, base, tot);
+                    piece_offsets<CW>(m, cf, base, tot);
                     written = rng_piece<CW>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
                 }
                 // own rows only: other threads read these cursors after the
                 // next scan
-                for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
+                for (u32 r = tid; r < cf; r += RNG_T) m.cur[r] = m.ce[r];
             } else {
                 // bisect by key: pieces [plo, phi) with at most CHUNK
                 // products, or a single monomial
@@ -688,10 +792,10 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                     u64 phi = rhi_k;
                     for (;;) {
                         u64 cnt_mine = 0;
-                        for (u32 r = r0; r < r1; r++) {
+                        for (u32 r = tid; r < cf; r += RNG_T) {
                             const u64 ar = A[r];
                             const u32 e = phi > ar ? gallop_up(m.Bs, cg, m.cur[r], phi - ar) : m.cur[r];
-                            jh[r - r0] = e;
+                            m.ce[r] = (uint16_t)e;
                             cnt_mine += row_counts(e - m.cur[r]);
                         }
                         u64 ptot;
@@ -699,18 +803,18 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                         const u64 PO = (u32)ptot;
                         if (PO <= R::CHUNK) {
                             if (PO) {
-                                piece_offsets<CW>(m, r0, r1, jh, pbase, ptot);
+                                piece_offsets<CW>(m, cf, pbase, ptot);
                                 written += rng_piece<CW>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
                             }
                             break;
                         }
                         if (phi - plo == 1) {
-                            written += rng_single<CW>(a, d, m, A, Ac, Bc, r0, r1, jh, plo, claim_r + written, ws);
+                            written += rng_single<CW>(a, d, m, A, Ac, Bc, cf, plo, claim_r + written, ws);
                             break;
                         }
                         phi = plo + (phi - plo) / 2;
                     }
-                    for (u32 r = r0; r < r1; r++) m.cur[r] = (uint16_t)jh[r - r0];
+                    for (u32 r = tid; r < cf; r += RNG_T) m.cur[r] = m.ce[r];
                     plo = phi;
                 }
             }

@@ -139,6 +139,29 @@ def test_batch_heavy_multiplicity():
     _check_against_oracle(prods[0], res[0][1])
 
 
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_batch_clustered_keys_take_the_radix_path(kind):
+    """Keys clustered inside a range's interval (64 x 64 products packed in a
+    small corner of a span of about 2^52) put more than 32 pairs into one
+    bucket, so the range kernel sorts those pieces by radix instead; one far
+    term of f stretches the span.  The result must still equal the oracle."""
+    import paper_1303_7425_gb300 as P
+    i = np.arange(64, dtype=np.uint32)
+    fe = np.stack([np.concatenate([i, [1 << 20]]), np.zeros(65, np.uint32)], axis=1).astype(np.uint32)
+    ge = np.stack([np.zeros(64, np.uint32), i], axis=1).astype(np.uint32)
+    st = polygen.Stream(77, 0)
+    if kind == "m61":
+        fc, gc = st.coef_m61(65), st.coef_m61(64)
+    else:
+        fc, gc = st.coef_i64(65, 1 << 40), st.coef_i64(64, 1 << 40)
+    w = polygen.Workload("cluster", 2, [32, 32], kind, polygen.Poly(fe, fc), polygen.Poly(ge, gc))
+    for opts in (dict(), dict(range_target=1024, ranges_per_item=2)):
+        prods = [_product(w)]
+        res, _ = P.batch_polymul(prods, **opts)
+        assert res[0][0] == 0
+        _check_against_oracle(prods[0], res[0][1])
+
+
 def test_graph_replay_recomputes_from_inputs():
     import paper_1303_7425_gb300 as P
     ws = _mixed_workloads(seed=9, count=12)
