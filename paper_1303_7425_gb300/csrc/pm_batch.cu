@@ -36,7 +36,6 @@ constexpr int PLAN_T = 1024;                      // B2 threads
 constexpr u32 PLAN_SAMPLES = 8192;
 constexpr int RNG_T = 512;                        // B3 threads
 constexpr u32 RNG_W = RNG_T / 32;
-constexpr u32 RNG_BS = BT_MAX_TERMS;               // g keys staged in shared memory (larger g: read via L1)
 constexpr int RNG_CTAS = 1;                        // B3 CTAs per SM
 // Products sorted per piece.  A product takes 8 + 8 (keys) + 2 + 2
 // (indexes) + 8 per coefficient word bytes of shared memory, so a batch
@@ -84,6 +83,7 @@ struct BArgs {
     u64 *bump;                    // output scratch counter
     u64 *skey, *scoef;            // output scratch; coefficient words per term: cw
     u32 cw;
+    u32 maxt;                     // largest operand of the batch, rounded up to 4096 or 8192 terms
     u32 target;                   // term products per range
     u32 per_item;                 // ranges per work item
     u64 rg_total;                 // range slots of the batch
@@ -362,14 +362,14 @@ struct RngSmem {
 // u16 arrays at offsets 0 and CROW.  The scan of the packed per-thread
 // counts (products in the low word, rows with products in the high word)
 // gives each thread's starts; rng_piece's first barrier publishes them.
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 struct Rng {
     static constexpr u32 CHUNK = rng_chunk(CW);
     static constexpr int IPT = CHUNK / RNG_T;
     static constexpr u32 LANE_MAX = (CHUNK / RNG_W + 31) / 32;  // products per lane of a piece
     static constexpr u32 CROW = CHUNK + 8;
     static constexpr u32 HIST_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
-    static constexpr size_t SMEM = (size_t)RNG_BS * 8 + BT_MAX_TERMS * 2 * 2 +
+    static constexpr size_t SMEM = (size_t)MAXT * 8 + MAXT * 2 * 2 +
                                    (size_t)CHUNK * (8 + 8 + 2 + 2 + 8 * CW) + (size_t)HIST_WORDS * 4;
     static_assert((CROW + CHUNK) * 2 <= CHUNK * 8, "row tables overflow the second key buffer");
     static_assert(CHUNK <= 65535 && CHUNK % RNG_T == 0, "16-bit product offsets, whole sort items per thread");
@@ -378,12 +378,12 @@ struct Rng {
     {
         RngSmem m;
         m.Bs = (u64 *)p;
-        m.kA = m.Bs + RNG_BS;
+        m.kA = m.Bs + MAXT;
         m.kB = m.kA + CHUNK;
         m.cv = m.kB + CHUNK;
         m.hist = (u32 *)(m.cv + CW * CHUNK);
         m.cur = (uint16_t *)(m.hist + HIST_WORDS);
-        m.iA = m.cur + BT_MAX_TERMS;
+        m.iA = m.cur + MAXT;
         m.iB = m.iA + CHUNK;
         m.ce = m.iB + CHUNK;
         return m;
@@ -395,10 +395,10 @@ __device__ __forceinline__ u64 row_counts(u32 cnt) { return (u64)cnt | ((u64)(cn
 // The piece's row tables (in kB), and the sort's bucket counts cleared for
 // the generation to fill.  Runs between the caller's scan and rng_piece's
 // first barrier; the previous piece no longer reads kB or hist by then.
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 cf, u64 base, u64 total)
 {
-    uint16_t *coff = (uint16_t *)m.kB, *crow = coff + Rng<CW>::CROW;
+    uint16_t *coff = (uint16_t *)m.kB, *crow = coff + Rng<CW, MAXT>::CROW;
     u32 pb = (u32)base, cb = (u32)(base >> 32);
     for (u32 r = threadIdx.x; r < cf; r += RNG_T) {
         const u32 cnt = (u32)m.ce[r] - m.cur[r];
@@ -423,10 +423,10 @@ __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 cf, u64 base, u64 
 // piece to the LSD radix sort instead.  On return m.kA/m.iA hold the sorted
 // pairs (the buffers may have swapped).  All threads call; ends with a
 // barrier.
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *ws)
 {
-    typedef Rng<CW> R;
+    typedef Rng<CW, MAXT> R;
     constexpr u32 PER = BUCKETS / RNG_T;
     static_assert(BUCKETS % RNG_T == 0, "buckets per thread");
     __shared__ u32 s_bmax;
@@ -516,11 +516,11 @@ __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *
 // claim_r being the range's output base as thread 0 holds it.  Returns the
 // terms written.  Ends without a barrier: the caller's next scan separates
 // this piece's reads of the shared buffers from the next piece's writes.
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                          u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws)
 {
-    typedef Rng<CW> R;
+    typedef Rng<CW, MAXT> R;
     const u32 tid = threadIdx.x;
     // a one-word batch holds mod-p products only
     const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
@@ -593,7 +593,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     }
     __syncthreads();
     const u32 n = O;
-    sort_piece<CW>(m, n, plo, span, shift, ws);
+    sort_piece<CW, MAXT>(m, n, plo, span, shift, ws);
     // segmented reduction: warp w owns the run heads in a contiguous
     // segment of the sorted pairs (a run may continue past it); positions
     // come from ballots and one block scan over the warps' counts
@@ -645,7 +645,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
 
 // sum of all products of a single-monomial piece with more than CHUNK
 // products; writes at most one term
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                           u32 cf, u64 key, u64 out, u64 *ws)
 {
@@ -694,10 +694,10 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
     return wrote;
 }
 
-template <u32 CW>
+template <u32 CW, u32 MAXT>
 __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
 {
-    typedef Rng<CW> R;
+    typedef Rng<CW, MAXT> R;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
     __shared__ u32 item;
@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
         const u64 *Bg = swap ? Fk : Gk, *Bc = swap ? Fc : Gc;
         // g's keys in shared memory when they fit, else read through L1
         m.Bs = (u64 *)smem;
-        if (cg <= RNG_BS) {
+        if (cg <= MAXT) {
             for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
         } else {
             m.Bs = const_cast<u64 *>(Bg);
@@ -778,8 +778,8 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             u64 written = 0;
             if (O <= R::CHUNK) {
                 if (O) {
-                    piece_offsets<CW>(m, cf, base, tot);
-                    written = rng_piece<CW>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
+                    piece_offsets<CW, MAXT>(m, cf, base, tot);
+                    written = rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
                 }
                 // own rows only: other threads read these cursors after the
                 // next scan
@@ -803,13 +803,13 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                         const u64 PO = (u32)ptot;
                         if (PO <= R::CHUNK) {
                             if (PO) {
-                                piece_offsets<CW>(m, cf, pbase, ptot);
-                                written += rng_piece<CW>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
+                                piece_offsets<CW, MAXT>(m, cf, pbase, ptot);
+                                written += rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
                             }
                             break;
                         }
                         if (phi - plo == 1) {
-                            written += rng_single<CW>(a, d, m, A, Ac, Bc, cf, plo, claim_r + written, ws);
+                            written += rng_single<CW, MAXT>(a, d, m, A, Ac, Bc, cf, plo, claim_r + written, ws);
                             break;
                         }
                         phi = plo + (phi - plo) / 2;
@@ -909,7 +909,7 @@ constexpr size_t PLAN_SMEM = (size_t)PLAN_SAMPLES * (8 + 8 + 2 + 2) + (PLAN_T / 
 
 struct BatchSizes {
     u64 op_total = 0, rg_total = 0, prod_total = 0;
-    u32 nitems = 0, cw = 1, target = 0, per_item = 0;
+    u32 nitems = 0, cw = 1, maxt = 4096, target = 0, per_item = 0;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -971,6 +971,7 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
         if (pk.nvars < 1 || pk.nvars > PM_MAX_VARS) throw Error(PM_EINVAL, "bad nvars");
         if (it.coef_kind != PM_COEF_M61 && it.coef_kind != PM_COEF_I64_ACC128) throw Error(PM_EINVAL, "bad kind");
         if (it.f.n > BT_MAX_TERMS || it.g.n > BT_MAX_TERMS) throw Error(PM_EINVAL, "operand above PM_BATCH_MAX_TERMS");
+        if (it.f.n > 4096 || it.g.n > 4096) z.maxt = BT_MAX_TERMS;
         if ((it.f.n && (!it.f.exps || !it.f.coefs)) || (it.g.n && (!it.g.exps || !it.g.coefs)))
             throw Error(PM_EINVAL, "null operand arrays");
         if (it.h.cap && (!it.h.keys || !it.h.coefs)) throw Error(PM_EINVAL, "null output arrays");
@@ -1037,18 +1038,47 @@ static BArgs carve_ws(unsigned char *base, u32 count, const BatchSizes &z)
     a.skey = (u64 *)(base + w.skey);
     a.scoef = (u64 *)(base + w.scoef);
     a.cw = z.cw;
+    a.maxt = z.maxt;
     a.target = z.target;
     a.per_item = z.per_item;
     a.rg_total = z.rg_total;
     return a;
 }
 
+// The range kernel's shared memory, and the smallest carve-out that holds
+// it, so that the rest of the SM's 256 KB stays L1 for the operand loads.
+template <u32 CW, u32 MAXT>
+static void set_ranges_smem()
+{
+    constexpr size_t bytes = Rng<CW, MAXT>::SMEM;
+    set_smem_b(kb_ranges<CW, MAXT>, bytes);
+    int dev = 0, per_sm = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    PM_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    if (per_sm <= 0) return;
+    // dynamic + static shared memory + the 1 KB the system reserves per block
+    cudaFuncAttributes fa;
+    PM_CUDA(cudaFuncGetAttributes(&fa, kb_ranges<CW, MAXT>));
+    const size_t need = bytes + fa.sharedSizeBytes + 1024;
+    int pct = (int)((need * 100 + (size_t)per_sm - 1) / (size_t)per_sm);
+    if (pct > 100) pct = 100;
+    PM_CUDA(cudaFuncSetAttribute(kb_ranges<CW, MAXT>, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+}
+
 static void set_batch_smem()
 {
     set_smem_b(kb_canon, CAN_SMEM);
     set_smem_b(kb_plan, PLAN_SMEM);
-    set_smem_b(kb_ranges<1>, Rng<1>::SMEM);
-    set_smem_b(kb_ranges<2>, Rng<2>::SMEM);
+    set_ranges_smem<1, 4096>();
+    set_ranges_smem<2, 4096>();
+    set_ranges_smem<1, BT_MAX_TERMS>();
+    set_ranges_smem<2, BT_MAX_TERMS>();
+}
+
+template <u32 CW, u32 MAXT>
+static void launch_ranges(const BArgs &a, int sm_count, cudaStream_t s)
+{
+    kb_ranges<CW, MAXT><<<sm_count * RNG_CTAS, RNG_T, Rng<CW, MAXT>::SMEM, s>>>(a);
 }
 
 // the four kernels of the pass (counters cleared first)
@@ -1060,10 +1090,14 @@ static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
     PM_CUDA(cudaGetLastError());
     kb_plan<<<a.count, PLAN_T, PLAN_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
-    if (a.cw == 1)
-        kb_ranges<1><<<sm_count * RNG_CTAS, RNG_T, Rng<1>::SMEM, s>>>(a);
-    else
-        kb_ranges<2><<<sm_count * RNG_CTAS, RNG_T, Rng<2>::SMEM, s>>>(a);
+    // operands of at most 4096 terms leave room for a larger L1
+    if (a.maxt <= 4096) {
+        if (a.cw == 1) launch_ranges<1, 4096>(a, sm_count, s);
+        else launch_ranges<2, 4096>(a, sm_count, s);
+    } else {
+        if (a.cw == 1) launch_ranges<1, BT_MAX_TERMS>(a, sm_count, s);
+        else launch_ranges<2, BT_MAX_TERMS>(a, sm_count, s);
+    }
     PM_CUDA(cudaGetLastError());
     kb_finish<<<a.count, FIN_T, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());

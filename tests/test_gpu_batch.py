@@ -162,6 +162,25 @@ def test_batch_clustered_keys_take_the_radix_path(kind):
         _check_against_oracle(prods[0], res[0][1])
 
 
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_batch_operands_above_4096_terms(kind):
+    """An operand above 4096 terms switches the range kernel to its layout
+    for up to PM_BATCH_MAX_TERMS terms; the small products beside it must
+    come out the same."""
+    import paper_1303_7425_gb300 as P
+    st = polygen.Stream(88, 0)
+    big = polygen.sparse_product(polygen.Stream(88, 1), 3, 6000, 40)
+    big.f.coefs = st.coef_m61(6000) if kind == "m61" else st.coef_i64(6000, 1 << 30)
+    big.g.coefs = st.coef_m61(40) if kind == "m61" else st.coef_i64(40, 1 << 30)
+    big.kind = kind
+    ws = [big] + [w for w in _mixed_workloads(seed=23, count=6) if w.kind == "m61"]
+    prods = [_product(w) for w in ws]
+    res, _ = P.batch_polymul(prods)
+    for pr, (status, n) in zip(prods, res):
+        assert status == 0
+        _check_against_oracle(pr, n)
+
+
 def test_graph_replay_recomputes_from_inputs():
     import paper_1303_7425_gb300 as P
     ws = _mixed_workloads(seed=9, count=12)
