@@ -26,8 +26,10 @@ namespace pm {
 
 constexpr int DT = 1024;          // threads per CTA
 constexpr int DW = DT / 32;       // warps
-constexpr int DRPT = 1;           // rows staged per thread and pass
+constexpr int DRPT = 1;           // table rows per thread
 constexpr int DROWS = DT * DRPT;  // rows staged per pass
+constexpr int DCAND = 2;          // candidate rows looked at per thread and pass
+static_assert(DCAND * DT < 4096, "kept-row count in 12 bits");
 
 // shared-memory row tables of one pass: per staged row a 16-byte record
 // (a_i as two words, rank of alpha_i minus the window start, first column
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
     acc.carve(smem);
     DTables t = carve_dtables(smem + (size_t)Acc<ACC>::slots * Acc<ACC>::bytes);
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    __shared__ u32 s_next;
+    __shared__ u32 s_next, s_cand;
     // inputs that no longer match a replayed plan could put products
     // outside the windows; such a replay computes nothing (the window
     // counts stay zero)
@@ -410,16 +412,20 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         const u32 *Elo = a.E + bw * na, *Ehi = Elo + na;
         __syncthreads();
 
-        for (u32 base = i0; base < i1; base += DROWS) {
-            // thread tid stages rows base + tid * DRPT + [0, DRPT); the
-            // records need the rows' offsets, so they are written after the
-            // scan
-            u32 lens[DRPT], jls[DRPT], ras[DRPT];
-            u64 cas[DRPT];
-            u64 len = 0;
+        // passes: each stages up to DROWS rows that have products in the
+        // window (about half of the rows reaching it by their bounds have
+        // none), taken in row order from the next DCAND * DT candidates
+        for (u32 cand = i0; cand < i1;) {
+            // thread tid looks at candidates cand + tid * DCAND + [0, DCAND);
+            // one scan counts the kept rows (low 12 bits) and their products
+            // (high bits); the records need the rows' offsets, so they are
+            // written after it
+            u32 lens[DCAND], jls[DCAND], ras[DCAND];
+            u64 cas[DCAND];
+            u64 packed = 0;
 #pragma unroll
-            for (int k = 0; k < DRPT; k++) {
-                const u32 i = base + tid * DRPT + k;
+            for (int k = 0; k < DCAND; k++) {
+                const u32 i = cand + tid * DCAND + k;
                 lens[k] = 0;
                 jls[k] = 0;
                 ras[k] = 0;
@@ -428,28 +434,44 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                     jls[k] = i < i1lo ? Elo[i] : 0u;
                     const u32 jh = i >= i0hi ? Ehi[i] : nb;
                     lens[k] = jh - jls[k];
+                }
+                if (lens[k]) {
                     ras[k] = (u32)__ldg(a.A + i) - (u32)lo;
                     cas[k] = __ldg(a.Ac + i);
+                    packed += ((u64)lens[k] << 12) | 1u;
                 }
-                len += lens[k];
             }
-            u64 total;
-            u64 ex = block_exclusive_scan(len, total, ws);
+            u64 ptot;
+            const u64 ex = block_exclusive_scan(packed, ptot, ws);
+            const u32 kept_all = (u32)(ptot & 4095u);
+            const bool cut = kept_all > (u32)DROWS;
+            u32 kept = (u32)(ex & 4095u);
+            u32 off = (u32)(ex >> 12);
 #pragma unroll
-            for (int k = 0; k < DRPT; k++) {
-                const u32 li = tid * DRPT + k;
-                t.off[li] = (u32)ex;
-                t.rec[li] = make_uint4((u32)cas[k], (u32)(cas[k] >> 32), ras[k], jls[k] - (u32)ex);
-                ex += lens[k];
+            for (int k = 0; k < DCAND; k++) {
+                if (lens[k]) {
+                    const u32 i = cand + tid * DCAND + k;
+                    if (kept < (u32)DROWS) {
+                        t.off[kept] = off;
+                        t.rec[kept] = make_uint4((u32)cas[k], (u32)(cas[k] >> 32), ras[k], jls[k] - off);
+                        off += lens[k];
+                    } else if (kept == (u32)DROWS) {
+                        // the first row that does not fit starts the next pass
+                        t.off[DROWS] = off;
+                        s_cand = i;
+                    }
+                    kept++;
+                }
             }
-            if (tid == 0) t.off[DROWS] = (u32)total;
-            const u32 nrows = min(i1 - base, (u32)DROWS);
+            if (!cut && tid == 0) t.off[kept_all] = (u32)(ptot >> 12);
             __syncthreads();
+            const u32 nrows = cut ? (u32)DROWS : kept_all;
+            const u32 next = cut ? s_cand : cand + DCAND * DT;
 
             // warp w takes a contiguous slice of the pass's products; each
             // lane runs two independent streams over its two halves so the
             // loads and multiplies of one overlap the latency of the other
-            const u32 tot = (u32)total;
+            const u32 tot = t.off[nrows];
             const u32 per_warp = ((tot + DW - 1) / DW + 63u) & ~63u;
             const u32 p0 = w * per_warp;
             const u32 p1 = min(p0 + per_warp, tot);
@@ -479,6 +501,7 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                 sb.p += 32;
             }
             __syncthreads();
+            cand = next;
         }
 
         // emit the window's non-zero slots in ascending order: warp w owns
