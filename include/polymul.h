@@ -118,7 +118,7 @@ typedef struct pm_options {
     uint32_t ranges_per_sm;    /* direct: groups per SM; sort: unused                 */
     int32_t accumulator;       /* PM_ACC_*; PM_ACC_LIMBS needs min(n_f, n_g) <= 65537 */
     uint32_t cost_row;         /* direct: group cost model, cost of one row of f
-                                  staged for a window, in term products (0 = 12)    */
+                                  reaching a window, in term products (0 = 3)       */
     uint32_t cost_window;      /* direct: cost of one window in term products
                                   (0 = 23000); the groups balance
                                   products + cost_row rows + cost_window windows    */

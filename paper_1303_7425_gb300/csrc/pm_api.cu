@@ -408,7 +408,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         const u32 Gn = (u32)G64;
         u32 l = 1;
         while ((u64)(l + 1) * (l + 1) < 256ull * Gn && l < 4096) l++;
-        const u32 crow = o.cost_row ? o.cost_row : 12u, cwin = o.cost_window ? o.cost_window : 23000u;
+        const u32 crow = o.cost_row ? o.cost_row : 3u, cwin = o.cost_window ? o.cost_window : 23000u;
         const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, slots,
                                       crow, cwin);
         okey = S.get<u64>(end - lo);

@@ -606,13 +606,13 @@ __global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__rest
 }
 
 // Every bucket also carries its share of the window costs.  A window of
-// `win` ranks starting at the bucket stages the rows of f whose products
+// `win` ranks starting at the bucket looks at the rows of f whose products
 // can land in it -- alpha_i in [x - beta_max, x + win - beta_min) -- and the
 // accumulate kernel's time per group measures as about
-//     products + cost_row (rows staged over its windows) + cost_window (windows)
-// in units of one term product, with cost_row 5 to 20 and cost_window
-// about 23000 (per-group timings of the dense workloads; 12 and 23000 by
-// default, the autotuner picks the weights per shape class).  K_b = cost_row rows + cost_window is
+//     products + cost_row (rows reaching its windows) + cost_window (windows)
+// in units of one term product (per-group timings of the dense workloads;
+// since the passes stage only rows with products, 3 and 23000 by default;
+// the autotuner picks the weights per shape class).  K_b = cost_row rows + cost_window is
 // a window's cost near bucket b; a bucket of bw ranks carries bw / win of
 // it (kw keeps K_b for the refinement below).
 // (Both histogram kernels run HB-thread blocks, one bucket per thread, and

@@ -129,8 +129,8 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
         for (u32 slots : {0u, 8192u}) add(PM_STRATEGY_DIRECT, slots, gps, PM_ACC_AUTO, 0);
     add(PM_STRATEGY_DIRECT, 0, 1, PM_ACC_WIDE, 0);
     for (u32 gps : {1u, 2u}) {
-        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 20, 50000);
-        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 3, 5000);
+        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 6, 12000);
+        add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 1, 8000);
     }
     // sort + reduce: chunk sizes; hashed windows
     for (u32 chunk : {2048u, 4096u}) add(PM_STRATEGY_SORT, 0, 0, PM_ACC_AUTO, chunk);
