@@ -115,13 +115,36 @@ __device__ __forceinline__ u32 walk_down(const K *B, u32 j, u64 x)
     return lo + lower_bound_k(B + lo, hi - lo, x);
 }
 
+// first index in [0, n) with a[i] >= x (n if none), by one warp: each round
+// the 32 lanes probe 32 evenly spaced points of the interval that holds the
+// answer, and the ballot of the probes below x narrows it 32-fold (three
+// dependent loads for 32k elements instead of fifteen).  All lanes call.
+template <class K>
+__device__ __forceinline__ u32 warp_lower_bound(const K *__restrict__ a, u32 n, u64 x)
+{
+    const u32 lane = threadIdx.x & 31;
+    u32 lo = 0, hi = n;  // the answer is in [lo, hi]
+    while (lo < hi) {
+        const u32 step = (hi - lo + 31) >> 5;
+        const u32 probe = lo + (lane + 1) * step - 1;
+        const bool below = probe < hi && (u64)a[probe] < x;
+        const u32 k = (u32)__popc(__ballot_sync(0xffffffffu, below));  // a prefix of the lanes
+        const u32 nhi = lo + (k + 1) * step - 1;
+        lo += k * step;
+        hi = nhi < hi ? nhi : hi;
+    }
+    return lo;
+}
+
 // FindEdge (Sec. 2) for the window boundaries: for boundary x = W[b] and
 // every row i that reaches it, E[b][i] = #{j : beta_j < x - alpha_i}.  Rows
 // below i0 (alpha_i + beta_max < x) have all n_b columns below x, rows from
 // i1 on (alpha_i + beta_min >= x) none; cnt[b] = #{(i, j) : gamma_ij < x}.
 // The row edges move left as i grows, so each thread walks a contiguous
 // chunk of rows as a staircase after one binary search; g's keys are
-// staged in shared memory when they fit.
+// staged in shared memory when they fit.  Warps 0 and 1 find i0 and i1
+// while the others stage g.  The grid is sized by an upper bound on the
+// boundaries; blocks past their count return at once.
 template <class K>
 __global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const K *__restrict__ B, u32 na, u32 nb,
                                                   const u64 *__restrict__ W, const u64 *__restrict__ nbound_minus1,
@@ -131,20 +154,24 @@ __global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
     __shared__ u32 rows[2];
-    K *Bs = (K *)smem;
-    if (stage)
-        for (u32 j = threadIdx.x; j < nb; j += DT) Bs[j] = B[j];
-    __syncthreads();
-    const K *Bp = stage ? Bs : B;
-    const u64 bmin = (u64)B[0], bmax = (u64)B[nb - 1];
     const u64 nbound = *nbound_minus1 + 1;
+    if (blockIdx.x >= nbound) return;
+    K *Bs = (K *)smem;
+    const u64 bmin = (u64)B[0], bmax = (u64)B[nb - 1];
+    const u32 w = threadIdx.x >> 5;
     for (u64 b = blockIdx.x; b < nbound; b += gridDim.x) {
         const u64 x = W[b];
-        if (threadIdx.x == 0) {
-            rows[0] = x > bmax ? lower_bound_k(A, na, x - bmax) : 0u;
-            rows[1] = x > bmin ? lower_bound_k(A, na, x - bmin) : 0u;
+        if (w == 0) {
+            const u32 r = x > bmax ? warp_lower_bound(A, na, x - bmax) : 0u;
+            if (threadIdx.x == 0) rows[0] = r;
+        } else if (w == 1) {
+            const u32 r = x > bmin ? warp_lower_bound(A, na, x - bmin) : 0u;
+            if (threadIdx.x == 32) rows[1] = r;
+        } else if (stage && b == blockIdx.x) {
+            for (u32 j = threadIdx.x - 64; j < nb; j += DT - 64) Bs[j] = B[j];
         }
         __syncthreads();
+        const K *Bp = stage ? Bs : B;
         const u32 i0 = rows[0], i1 = rows[1];
         u32 *Eb = E + b * na;
         u64 sum = 0;
@@ -706,12 +733,15 @@ static_assert(GC_BUCKETS % HB == 0, "whole histogram blocks per cut block");
 __device__ __forceinline__ void cut_emit(u64 a, u64 b, u64 i, u64 W, u32 G, u64 lo, u64 end, u64 bw,
                                          u64 *__restrict__ gb)
 {
-    // m with a < floor(W m / G) <= b: from ceil((a + 1) G / W) while in range
-    u64 m = (u64)(((unsigned __int128)(a + 1) * G + W - 1) / W);
+    // m with a < floor(W m / G) <= b: from ceil((a + 1) G / W) while in
+    // range; in 64 bits when W G fits (b < W, so (a + 1) G does too)
+    const bool narrow = W <= ~0ull / ((u64)G + 1);
+    u64 m = narrow ? ((a + 1) * G + W - 1) / W : (u64)(((unsigned __int128)(a + 1) * G + W - 1) / W);
     u64 v = lo + i * bw;
     if (v > end) v = end;
     for (; m < G; m++) {
-        if ((u64)(((unsigned __int128)W * m) / G) > b) break;
+        const u64 t = narrow ? W * m / G : (u64)(((unsigned __int128)W * m) / G);
+        if (t > b) break;
         gb[m] = v;
     }
 }
