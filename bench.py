@@ -228,9 +228,27 @@ def probe_peak(P, torch):
     return best
 
 
+def kernel_source_hash(source: str, region=None):
+    """sha256 (16 hex digits) of a kernel's source text: the whole file, or
+    the text from the line starting with region[0] up to (not including) the
+    line starting with region[1]."""
+    path = os.path.join(ROOT, "paper_1303_7425_gb300", "csrc", source)
+    try:
+        text = open(path, encoding="utf-8").read()
+    except OSError:
+        return None
+    if region:
+        a = text.find("\n" + region[0])
+        b = text.find("\n" + region[1], a + 1)
+        if a < 0 or b < 0:
+            return None
+        text = text[a + 1:b + 1]
+    return hashlib.sha256(text.encode("utf-8")).hexdigest()[:16]
+
+
 def traffic_for(kernel: str, workload_key: str):
     """dram bytes per launch from the committed ncu summary, or None if the
-    kernel source changed since the counters were taken."""
+    kernel's source changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
@@ -240,12 +258,8 @@ def traffic_for(kernel: str, workload_key: str):
     ent = d.get(workload_key)
     if not ent or ent.get("kernel") != kernel:
         return None
-    src = os.path.join(ROOT, "paper_1303_7425_gb300", "csrc", ent.get("source", "pm_direct.cu"))
-    try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
-        return None
-    return ent.get("dram_bytes_per_launch") if h == ent.get("source_sha256_16") else None
+    h = kernel_source_hash(ent.get("source", "pm_direct.cu"), ent.get("region"))
+    return ent.get("dram_bytes_per_launch") if h and h == ent.get("source_sha256_16") else None
 
 
 def e2e_product(P, torch, w, steps, warmup):

@@ -37,6 +37,24 @@ __device__ __forceinline__ u64 m61_mul_lazy(u64 a, u64 b)
     return (lo & P61) + ((hi << 3) | (lo >> 61));
 }
 
+// a b mod p from 31-bit splits, four 32 x 32 -> 64 multiplies.  With
+// a = ah 2^31 + al and b = bh 2^31 + bl (al, bl < 2^31; ah, bh < 2^30),
+//     a b = ah bh 2^62 + (ah bl + al bh) 2^31 + al bl,
+// and 2^62 = 2, 2^61 = 1 (mod p); the middle sum m < 2^62 splits as
+// m = mh 2^30 + ml (ml < 2^30), so m 2^31 = mh + ml 2^31 (mod p):
+//     a b = al bl + 2 ah bh + mh + ml 2^31  (mod p), the sum < 2^64.
+// as = al | ah << 32 (m61_split_row), bs = bl | (2 bh) << 32
+// (m61_split_col): the doubled bh folds the 2 into one multiply.
+__device__ __forceinline__ u64 m61_split_row(u64 a) { return (a & 0x7FFFFFFFull) | ((a >> 31) << 32); }
+__device__ __forceinline__ u64 m61_split_col(u64 b) { return (b & 0x7FFFFFFFull) | ((b >> 31) << 33); }
+__device__ __forceinline__ u64 m61_mul_split(u64 as, u64 bs)
+{
+    const u32 al = (u32)as, ah = (u32)(as >> 32), bl = (u32)bs, bh2 = (u32)(bs >> 32);
+    const u64 t = (u64)al * bl + (u64)ah * bh2;
+    const u64 m = (u64)ah * bl + (u64)al * (bh2 >> 1);
+    return t + (m >> 30) + ((m & 0x3FFFFFFFull) << 31);
+}
+
 // any 64-bit x -> [0, p)
 __device__ __forceinline__ u64 m61_reduce(u64 x)
 {

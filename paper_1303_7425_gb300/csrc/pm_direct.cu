@@ -299,6 +299,26 @@ struct Acc {
             if (ACC == ACC_I192) w[2 * slots + s] = 0;
         }
     }
+    // the product of a row coefficient and a column coefficient: for the
+    // mod-p accumulators both come split (m61_split_row / m61_split_col)
+    // and the product is m61_mul_split's (< 2^64; the limbs and the wrap
+    // count take any 64-bit value); the integer kinds take them as they are
+    __device__ __forceinline__ void add_split(u32 s, u64 a, u64 b)
+    {
+        if (ACC == ACC_W64) {
+            const u64 v = m61_mul_split(a, b);
+            const u64 old = atomicAdd(&w[s], v);
+            atomicAdd(&c[s], (u32)(old + v < old));
+        } else if (ACC == ACC_L16) {
+            const u64 v = m61_mul_split(a, b);
+            atomicAdd(&c[s], (u32)v & 0xFFFFu);
+            atomicAdd(&c[slots + s], (u32)(v >> 16) & 0xFFFFu);
+            atomicAdd(&c[2 * slots + s], (u32)(v >> 32) & 0xFFFFu);
+            atomicAdd(&c[3 * slots + s], (u32)(v >> 48));
+        } else {
+            add(s, a, b);
+        }
+    }
     __device__ __forceinline__ void add(u32 s, u64 a, u64 b)
     {
         if (ACC == ACC_W64) {
@@ -465,6 +485,7 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                 if (lens[k]) {
                     ras[k] = (u32)__ldg(a.A + i) - (u32)lo;
                     cas[k] = __ldg(a.Ac + i);
+                    if (ACC == ACC_W64 || ACC == ACC_L16) cas[k] = m61_split_row(cas[k]);
                     packed += ((u64)lens[k] << 12) | 1u;
                 }
             }
@@ -522,8 +543,8 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                     bb = __ldg(a.B32 + jb);
                     gbv = __ldg(a.Bc + jb);
                 }
-                if (va) acc.add(sa.ra + ba, sa.ca, ga);
-                if (vb) acc.add(sb.ra + bb, sb.ca, gbv);
+                if (va) acc.add_split(sa.ra + ba, sa.ca, ga);
+                if (vb) acc.add_split(sb.ra + bb, sb.ca, gbv);
                 sa.p += 32;
                 sb.p += 32;
             }
@@ -569,6 +590,13 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
         if (tid == 0) a.ucount[bw] = wtot;
         __syncthreads();
     }
+}
+
+// g's coefficients (residues mod p) in the split form of m61_mul_split
+__global__ void k_split_col(const u64 *__restrict__ b, u64 *__restrict__ out, u32 n)
+{
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = m61_split_col(b[i]);
 }
 
 // Order of the windows for the persistent accumulate kernel: descending
@@ -906,8 +934,15 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     k_window_order<<<1, 1024, 0, c.s>>>(a.cnt, a.i0s, a.i1s, wpos + G, cost_row, cost_window, a.order);
     PM_LAUNCHED(c);
 
-    // accumulate: persistent CTAs, one per SM
+    // accumulate: persistent CTAs, one per SM; mod-p kinds read g's
+    // coefficients split for m61_mul_split
     const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
+    if (acc == ACC_W64 || acc == ACC_L16) {
+        u64 *bs = S.get<u64>(a.nb);
+        k_split_col<<<(a.nb + 255) / 256, 256, 0, c.s>>>(a.Bc, bs, a.nb);
+        PM_LAUNCHED(c);
+        a.Bc = bs;
+    }
     const size_t bytes = (size_t)acc_stride(acc_bytes(acc)) * acc_bytes(acc) + DTABLE_BYTES;
     const unsigned grid = (unsigned)(nbmax < (u64)c.sm_count ? nbmax : (u64)c.sm_count);
     if (ev_k0) PM_CUDA(cudaEventRecord(ev_k0, c.s));
