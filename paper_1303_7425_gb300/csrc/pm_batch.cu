@@ -230,12 +230,16 @@ __global__ void __launch_bounds__(PLAN_T) kb_plan(BArgs a)
         }
         return;
     }
-    // Sec. 5 grid with about R points: steps floor(n/l) clamped to >= 1,
-    // alternate rows shifted by floor(n_b / 2l), plus the last row and column
-    // (l+1)^2 ~ R points; floor-divided steps can give more, so shrink l
-    // until the whole grid fits the sample buffer
+    // Sec. 5 grid: steps floor(n/l) clamped to >= 1, alternate rows shifted
+    // by floor(n_b / 2l), plus the last row and column, (l+1)^2 points.
+    // About four points per range where the sample buffer allows (the
+    // splitters are every fourth order statistic then, and fewer ranges
+    // exceed the shared-memory chunk than with one point per range);
+    // floor-divided steps can give more, so shrink l until the whole grid
+    // fits the sample buffer
+    const u64 Rs = 4 * R < PLAN_SAMPLES ? 4 * R : PLAN_SAMPLES;
     u32 l = 1;
-    while ((u64)(l + 2) * (l + 2) <= R) l++;
+    while ((u64)(l + 2) * (l + 2) <= Rs) l++;
     u32 si, sj, Rr, Cc;
     u64 ns64;
     for (;;) {
