@@ -569,7 +569,8 @@ def run_ours(args):
                 "range_step_ms": statistics.mean(s["ms_range_step"] for s in stats),
                 "kernel_ms": kern_ms, "kernel_share_of_step": kern_ms / ms_step,
                 "peak_source": "measured on this GPU in this run: register-only M61 multiply-accumulate probe "
-                               "(key add + 61x61 product + Mersenne fold + modular add per term product)"}
+                               "(key add + 61x61 product + Mersenne fold + modular add per term product; the "
+                               "64x64->128 form, which measures faster in this probe than the 31-bit split form)"}
         if planned:
             e2e_ms, h2d, d2h = e2e_plan(P, torch, w, max(5, min(args.steps, 50)), 3)
         else:
