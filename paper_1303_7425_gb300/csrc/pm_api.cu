@@ -6,6 +6,7 @@
 // steps; every array the product touches is processed by the kernels.
 #include <cstddef>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 
@@ -102,6 +103,60 @@ struct Small {  // host mirror of the small device block
     u32 pad;
     u64 count_f, count_g, maxabs_f, maxabs_g;
     u64 fl_f[2], fl_g[2];  // first and last canonical key of f and g
+};
+
+// A second stream for the steps on g that do not wait for f's (input
+// maxima, canonical form, statistics, ranks): forked from the call's stream
+// and joined back with events, so in a plan's capture they become parallel
+// branches of the graph.  Its scratch is allocated on the side stream and
+// freed there only after everything the call's stream enqueued, and the
+// side stream is joined back once more after the frees.  One non-blocking
+// stream per host thread and device.
+static cudaStream_t side_stream()
+{
+    static thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    PM_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error(PM_ECUDA, "device index out of range");
+    if (!streams[dev]) PM_CUDA(cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking));
+    return streams[dev];
+}
+
+struct Side {
+    Ctx &main;
+    Ctx c;
+    std::unique_ptr<Scratch> S;
+    cudaEvent_t ev = nullptr;
+    explicit Side(Ctx &m) : main(m), c(m)
+    {
+        c.launches = 0;
+        c.syncs = 0;
+        c.s = side_stream();
+        S.reset(new Scratch(c.s));
+        PM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    void fork()
+    {
+        PM_CUDA(cudaEventRecord(ev, main.s));
+        PM_CUDA(cudaStreamWaitEvent(c.s, ev, 0));
+    }
+    void join()
+    {
+        PM_CUDA(cudaEventRecord(ev, c.s));
+        PM_CUDA(cudaStreamWaitEvent(main.s, ev, 0));
+        main.launches += c.launches;
+        c.launches = 0;
+    }
+    ~Side()
+    {
+        // error paths too: no throwing here
+        cudaEventRecord(ev, main.s);
+        cudaStreamWaitEvent(c.s, ev, 0);
+        S.reset();
+        cudaEventRecord(ev, c.s);
+        cudaStreamWaitEvent(main.s, ev, 0);
+        cudaEventDestroy(ev);
+    }
 };
 
 static void read_small(Ctx &c, Small &h, const Small *d)
@@ -231,6 +286,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     Small *ds = rec ? rec->d_small : S.get<Small>(1);
     PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
     if (capture) PM_CUDA(cudaMemsetAsync(rec->d_flag, 0, sizeof(u32), c.s));
+    Side side(c);  // g's steps; destroyed before S
     auto finish = [&](u64 n_out) {
         h->n = n_out;
         stats.n_out = n_out;
@@ -244,8 +300,10 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
 
     // K-a (1): input guard bits and the raw exponent box            [sync 1]
     Layout L = base_layout(*pk);
+    side.fork();
     input_maxima(c, *f, L, ds->maxe_f, &ds->status);
-    input_maxima(c, *g, L, ds->maxe_g, &ds->status);
+    input_maxima(side.c, *g, L, ds->maxe_g, &ds->status);
+    side.join();
     fetch_small(c, hs, ds, rec);
     if (hs.status & ST_EXP_OVERFLOW) throw Error(PM_EEXP_OVERFLOW, "input exponent reaches its guard bit");
     if (f->n == 0 || g->n == 0) return finish(0);
@@ -269,18 +327,21 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         const u64 box_f = set_box(own_f, hs.maxe_f, zero);
         const u64 box_g = set_box(own_g, hs.maxe_g, zero);
         auto dense_ok = [](u64 box, u64 n) { return box <= (1ull << 26) && box <= 16 * n + 65536; };
+        side.fork();
         if (dense_ok(box_f, f->n))
             canonicalize_dense(c, S, *f, own_f, box_f, kind, F, &ds->status, &ds->count_f, abort);
         else
             canonicalize(c, S, *f, raw, raw_box, kind, F, &ds->status, &ds->count_f);
         if (dense_ok(box_g, g->n))
-            canonicalize_dense(c, S, *g, own_g, box_g, kind, G, &ds->status, &ds->count_g, abort);
+            canonicalize_dense(side.c, *side.S, *g, own_g, box_g, kind, G, &ds->status, &ds->count_g, abort);
         else
-            canonicalize(c, S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
+            canonicalize(side.c, *side.S, *g, raw, raw_box, kind, G, &ds->status, &ds->count_g);
     }
-    PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * 2 * PM_MAX_VARS, c.s));
+    PM_CUDA(cudaMemsetAsync(ds->maxe_f, 0, sizeof(u32) * PM_MAX_VARS, c.s));
+    PM_CUDA(cudaMemsetAsync(ds->maxe_g, 0, sizeof(u32) * PM_MAX_VARS, side.c.s));
     operand_stats(c, F, f->n, &ds->count_f, L, kind, ds->maxe_f, &ds->maxabs_f, ds->fl_f);
-    operand_stats(c, G, g->n, &ds->count_g, L, kind, ds->maxe_g, &ds->maxabs_g, ds->fl_g);
+    operand_stats(side.c, G, g->n, &ds->count_g, L, kind, ds->maxe_g, &ds->maxabs_g, ds->fl_g);
+    side.join();
     fetch_small(c, hs, ds, rec);
     if (hs.status & ST_COEF_BOUND) throw Error(PM_ECOEF_BOUND, "repeated input monomial leaves int64");
     F.n = hs.count_f;
@@ -398,8 +459,10 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         // K-b: ranks, grid sample, groups (no host sync)
         u32 *g32 = S.get<u32>(G.n);
         u32 *f32 = box <= 0xFFFFFFFFull ? S.get<u32>(F.n) : nullptr;
+        side.fork();
         operand_ranks(c, F, L, f32);
-        operand_ranks(c, G, L, g32);
+        operand_ranks(side.c, G, L, g32);
+        side.join();
         const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
         const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
         const u32 gps = o.ranges_per_sm ? o.ranges_per_sm : 1;

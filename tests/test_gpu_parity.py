@@ -100,6 +100,30 @@ def test_c2_full_size(kind, acc):
     _sampled_check(w, gpu)
 
 
+@pytest.mark.parametrize("nf,ng,slots", [(5000, 5000, 0), (3000, 2500, 1024), (2100, 40, 0)])
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_direct_every_row_has_products(nf, ng, slots, kind):
+    """Univariate dense operands: every row that reaches a window has
+    products in it, so a pass of the accumulate kernel finds more rows with
+    products among its 2048 candidates than its 1024-row table holds and
+    the next pass starts at the first row left out.  Ragged sizes, a small
+    window and one short operand cover the pass ends."""
+    st = polygen.Stream(4321, nf + ng)
+    fe = np.arange(nf, dtype=np.uint32).reshape(-1, 1)
+    ge = np.arange(ng, dtype=np.uint32)[::-1].copy().reshape(-1, 1)
+    if kind == "m61":
+        fc, gc = st.coef_m61(nf), st.coef_m61(ng)
+    else:
+        fc, gc = st.coef_i64(nf, 1 << 30), st.coef_i64(ng, 1 << 30)
+    w = polygen.Workload("uni", 1, [16], kind, polygen.Poly(fe, fc), polygen.Poly(ge, gc))
+    opts = dict(strategy="direct")
+    if slots:
+        opts["slots"] = slots
+    gpu = run_gpu(w.field_bits, kind, fe, fc, ge, gc, **opts)
+    assert gpu[2]["strategy"] == "direct"
+    assert_same(gpu, _oracle(w), w.field_bits)
+
+
 def test_c3_reduced_exact():
     w = polygen.workload_c3(n=3000)
     ref = _oracle(w)
