@@ -748,30 +748,22 @@ __global__ void __launch_bounds__(HB) k_hist_narrow(const u64 *__restrict__ gb, 
 
 // Group boundaries from the bucket costs: with c_i the cost of the buckets
 // below i (c_0 = 0, c_nbk = W), group m (0 < m < G) starts at bucket
-// i(m) = the first i with c_i >= floor(W m / G), i.e. at lo + i(m) bw (at
-// most end); gb[0] = lo and gb[G] = end.  One pass: each block takes GC_PER
-// consecutive buckets per thread, finds the cost below its first bucket
-// from the histogram kernels' per-block sums, scans its own buckets, and
-// the bucket i - 1 whose interval (c_{i-1}, c_i] holds floor(W m / G)
-// writes gb[m].
+// i(m) = the first i with c_i >= t_m = floor(W m / G), i.e. at lo + i(m) bw
+// (at most end); gb[0] = lo and gb[G] = end.  One pass: block b takes
+// GC_BUCKETS consecutive buckets [K0, K1), finds c_K0 from the histogram
+// kernels' per-block sums, scans its buckets into shared memory, and owns
+// the groups whose target falls in (c_K0, c_K1] (block 0 also those with
+// t_m = 0): two divisions per block give their range of m, one per group
+// its target, and a binary search over the block's scanned costs its
+// bucket.
 constexpr int GC_T = 1024, GC_PER = 4;
 constexpr u32 GC_BUCKETS = GC_T * GC_PER;
 static_assert(GC_BUCKETS % HB == 0, "whole histogram blocks per cut block");
 
-__device__ __forceinline__ void cut_emit(u64 a, u64 b, u64 i, u64 W, u32 G, u64 lo, u64 end, u64 bw,
-                                         u64 *__restrict__ gb)
+// floor(x y / z) and ceil(x y / z) without overflow of x y
+__device__ __forceinline__ u64 muldiv_floor(u64 x, u64 y, u64 z)
 {
-    // m with a < floor(W m / G) <= b: from ceil((a + 1) G / W) while in
-    // range; in 64 bits when W G fits (b < W, so (a + 1) G does too)
-    const bool narrow = W <= ~0ull / ((u64)G + 1);
-    u64 m = narrow ? ((a + 1) * G + W - 1) / W : (u64)(((unsigned __int128)(a + 1) * G + W - 1) / W);
-    u64 v = lo + i * bw;
-    if (v > end) v = end;
-    for (; m < G; m++) {
-        const u64 t = narrow ? W * m / G : (u64)(((unsigned __int128)W * m) / G);
-        if (t > b) break;
-        gb[m] = v;
-    }
+    return (u64)(((unsigned __int128)x * y) / z);
 }
 
 __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist, const u64 *__restrict__ part,
@@ -779,7 +771,10 @@ __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist
                                                     u64 *__restrict__ gb)
 {
     __shared__ u64 ws[32];
+    __shared__ u64 cs[GC_BUCKETS + 1];  // cs[j] = c_{K0 + j}
     const u32 tid = threadIdx.x;
+    const u64 K0 = (u64)blockIdx.x * GC_BUCKETS;
+    const u32 nloc = (u32)(nbk - K0 < GC_BUCKETS ? nbk - K0 : GC_BUCKETS);
     const u32 pb = blockIdx.x * (GC_BUCKETS / HB);  // histogram blocks before this block's buckets
     u64 below = 0, all = 0;
     for (u32 q = tid; q < nparts; q += GC_T) {
@@ -790,27 +785,50 @@ __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist
     u64 W, base;
     block_exclusive_scan(all, W, ws);
     block_exclusive_scan(below, base, ws);
-    const u64 k0 = (u64)blockIdx.x * GC_BUCKETS + (u64)tid * GC_PER;
     u64 h[GC_PER];
     u64 mine = 0;
 #pragma unroll
     for (int t = 0; t < GC_PER; t++) {
-        h[t] = k0 + t < nbk ? hist[k0 + t] : 0;
+        const u32 j = tid * GC_PER + t;
+        h[t] = j < nloc ? hist[K0 + j] : 0;
         mine += h[t];
     }
     u64 tot;
-    u64 c = base + block_exclusive_scan(mine, tot, ws);  // c_{k0}
-    if (W == 0) return;
+    u64 c = base + block_exclusive_scan(mine, tot, ws);
 #pragma unroll
     for (int t = 0; t < GC_PER; t++) {
-        if (k0 + t < nbk) cut_emit(c, c + h[t], k0 + t + 1, W, G, lo, end, bw, gb);
+        const u32 j = tid * GC_PER + t;
+        if (j < nloc) cs[j] = c;
         c += h[t];
     }
+    if (tid == 0) cs[nloc] = base + tot;
     if (blockIdx.x == 0 && tid == 0) {
         gb[0] = lo;
         gb[G] = end;
-        // floor(W m / G) <= c_0 = 0: i(m) = 0
-        for (u64 m = 1; m < G && (u64)(((unsigned __int128)W * m) / G) == 0; m++) gb[m] = lo;
+    }
+    __syncthreads();
+    if (W == 0) return;
+    // groups of this block: t_m in (c_K0, c_K1], and t_m = 0 in block 0
+    const u64 cK0 = cs[0], cK1 = cs[nloc];
+    u64 m_lo = blockIdx.x == 0 ? 1 : (u64)(((unsigned __int128)(cK0 + 1) * G + W - 1) / W);
+    u64 m_hi = (u64)(((unsigned __int128)(cK1 + 1) * G - 1) / W);  // last m with t_m <= c_K1
+    if (m_lo < 1) m_lo = 1;
+    if (m_hi > (u64)G - 1) m_hi = (u64)G - 1;
+    for (u64 m = m_lo + tid; m <= m_hi; m += GC_T) {
+        const u64 tm = muldiv_floor(W, m, G);
+        // first j in [0, nloc] with cs[j] >= tm; the bucket index is K0 + j
+        u32 a = 0, len = nloc + 1;
+        while (len > 0) {
+            const u32 half = len >> 1;
+            if (cs[a + half] < tm) {
+                a += half + 1;
+                len -= half + 1;
+            } else {
+                len = half;
+            }
+        }
+        u64 v = lo + (K0 + a) * bw;
+        gb[m] = v > end ? end : v;
     }
 }
 
