@@ -142,14 +142,17 @@ __device__ __forceinline__ u32 warp_lower_bound(const K *__restrict__ a, u32 n, 
 // i1 on (alpha_i + beta_min >= x) none; cnt[b] = #{(i, j) : gamma_ij < x}.
 // The row edges move left as i grows, so each thread walks a contiguous
 // chunk of rows as a staircase after one binary search; g's keys are
-// staged in shared memory when they fit.  Warps 0 and 1 find i0 and i1
-// while the others stage g.  The grid is sized by an upper bound on the
-// boundaries; blocks past their count return at once.
+// staged in shared memory when they fit, and so are the row edges, which
+// then go out with coalesced stores (a thread's chunk of rows would give
+// each lane a different line).  Warps 0 and 1 find i0 and i1 while the
+// others stage g.  The grid is sized by an upper bound on the boundaries;
+// blocks past their count return at once.
 template <class K>
 __global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const K *__restrict__ B, u32 na, u32 nb,
                                                   const u64 *__restrict__ W, const u64 *__restrict__ nbound_minus1,
                                                   u32 *__restrict__ E, u32 *__restrict__ i0s,
-                                                  u32 *__restrict__ i1s, u64 *__restrict__ cnt, u32 stage)
+                                                  u32 *__restrict__ i1s, u64 *__restrict__ cnt, u32 stage,
+                                                  u32 stage_e)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
@@ -157,6 +160,7 @@ __global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const
     const u64 nbound = *nbound_minus1 + 1;
     if (blockIdx.x >= nbound) return;
     K *Bs = (K *)smem;
+    u32 *Es = (u32 *)(smem + (stage ? ((size_t)nb * sizeof(K) + 15) / 16 * 16 : 0));
     const u64 bmin = (u64)B[0], bmax = (u64)B[nb - 1];
     const u32 w = threadIdx.x >> 5;
     for (u64 b = blockIdx.x; b < nbound; b += gridDim.x) {
@@ -174,22 +178,26 @@ __global__ void __launch_bounds__(DT) k_find_edge(const K *__restrict__ A, const
         const K *Bp = stage ? Bs : B;
         const u32 i0 = rows[0], i1 = rows[1];
         u32 *Eb = E + b * na;
+        u32 *Ew = stage_e ? Es : Eb;  // row i at Ew[i - eo]: Es holds rows [i0, i1)
+        const u32 eo = stage_e ? i0 : 0u;
         u64 sum = 0;
         const u32 per = (i1 - i0 + DT - 1) / DT;
         const u32 r0 = i0 + threadIdx.x * per;
         const u32 r1 = min(r0 + per, i1);
         if (r0 < r1) {
             u32 j = lower_bound_k(Bp, nb, x - (u64)A[r0]);
-            Eb[r0] = j;
+            Ew[r0 - eo] = j;
             sum = j;
             for (u32 i = r0 + 1; i < r1; i++) {
                 j = walk_down(Bp, j, x - (u64)A[i]);
-                Eb[i] = j;
+                Ew[i - eo] = j;
                 sum += j;
             }
         }
         u64 total;
-        block_exclusive_scan(sum, total, ws);
+        block_exclusive_scan(sum, total, ws);  // its barriers publish Es
+        if (stage_e)
+            for (u32 i = i0 + threadIdx.x; i < i1; i += DT) Eb[i] = Es[i - i0];
         if (threadIdx.x == 0) {
             cnt[b] = total + (u64)i0 * nb;
             i0s[b] = i0;
@@ -756,14 +764,16 @@ __global__ void __launch_bounds__(HB) k_hist_narrow(const u64 *__restrict__ gb, 
 // t_m = 0): two divisions per block give their range of m, one per group
 // its target, and a binary search over the block's scanned costs its
 // bucket.
-constexpr int GC_T = 1024, GC_PER = 4;
+constexpr int GC_T = 256, GC_PER = 4;
 constexpr u32 GC_BUCKETS = GC_T * GC_PER;
 static_assert(GC_BUCKETS % HB == 0, "whole histogram blocks per cut block");
 
-// floor(x y / z) and ceil(x y / z) without overflow of x y
-__device__ __forceinline__ u64 muldiv_floor(u64 x, u64 y, u64 z)
+// floor((x y + a) / z) without overflow of x y + a; 64-bit arithmetic when
+// it cannot overflow (a 128-bit division is a long software routine)
+__device__ __forceinline__ u64 muldiv_floor(u64 x, u64 y, u64 a, u64 z)
 {
-    return (u64)(((unsigned __int128)x * y) / z);
+    if (y == 0 || x <= (~0ull - a) / y) return (x * y + a) / z;
+    return (u64)(((unsigned __int128)x * y + a) / z);
 }
 
 __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist, const u64 *__restrict__ part,
@@ -776,15 +786,15 @@ __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist
     const u64 K0 = (u64)blockIdx.x * GC_BUCKETS;
     const u32 nloc = (u32)(nbk - K0 < GC_BUCKETS ? nbk - K0 : GC_BUCKETS);
     const u32 pb = blockIdx.x * (GC_BUCKETS / HB);  // histogram blocks before this block's buckets
+    // the cost below the block and the total, reduced together (one
+    // barrier), while the block's own buckets load
+    __shared__ u64 red[2][GC_T / 32];
     u64 below = 0, all = 0;
     for (u32 q = tid; q < nparts; q += GC_T) {
         const u64 v = part[q];
         all += v;
         if (q < pb) below += v;
     }
-    u64 W, base;
-    block_exclusive_scan(all, W, ws);
-    block_exclusive_scan(below, base, ws);
     u64 h[GC_PER];
     u64 mine = 0;
 #pragma unroll
@@ -792,6 +802,22 @@ __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist
         const u32 j = tid * GC_PER + t;
         h[t] = j < nloc ? hist[K0 + j] : 0;
         mine += h[t];
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        all += __shfl_xor_sync(0xffffffffu, all, d);
+        below += __shfl_xor_sync(0xffffffffu, below, d);
+    }
+    if ((tid & 31) == 0) {
+        red[0][tid >> 5] = all;
+        red[1][tid >> 5] = below;
+    }
+    __syncthreads();
+    u64 W = 0, base = 0;
+#pragma unroll
+    for (int q = 0; q < GC_T / 32; q++) {
+        W += red[0][q];
+        base += red[1][q];
     }
     u64 tot;
     u64 c = base + block_exclusive_scan(mine, tot, ws);
@@ -810,12 +836,13 @@ __global__ void __launch_bounds__(GC_T) k_group_cut(const u64 *__restrict__ hist
     if (W == 0) return;
     // groups of this block: t_m in (c_K0, c_K1], and t_m = 0 in block 0
     const u64 cK0 = cs[0], cK1 = cs[nloc];
-    u64 m_lo = blockIdx.x == 0 ? 1 : (u64)(((unsigned __int128)(cK0 + 1) * G + W - 1) / W);
-    u64 m_hi = (u64)(((unsigned __int128)(cK1 + 1) * G - 1) / W);  // last m with t_m <= c_K1
+    u64 m_lo = blockIdx.x == 0 ? 1 : muldiv_floor(cK0 + 1, G, W - 1, W);
+    // last m with t_m <= c_K1: floor(((c + 1) G - 1) / W) = ceil((c + 1) G / W) - 1
+    u64 m_hi = muldiv_floor(cK1 + 1, G, W - 1, W) - 1;
     if (m_lo < 1) m_lo = 1;
     if (m_hi > (u64)G - 1) m_hi = (u64)G - 1;
     for (u64 m = m_lo + tid; m <= m_hi; m += GC_T) {
-        const u64 tm = muldiv_floor(W, m, G);
+        const u64 tm = muldiv_floor(W, m, 0, G);
         // first j in [0, nloc] with cs[j] >= tm; the bucket index is K0 + j
         u32 a = 0, len = nloc + 1;
         while (len > 0) {
@@ -927,18 +954,26 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 
     // FindEdge at every boundary
     const unsigned fgrid = (unsigned)(nbmax < (u64)c.sm_count * 4 ? nbmax : (u64)c.sm_count * 4);
+    // g's keys in shared memory when they fit in 200 KB, the row edges too
+    // when both fit (two CTAs of 1024 threads share an SM up to ~113 KB each)
+    auto fe_smem = [&](size_t kbytes, u32 &stage, u32 &stage_e) {
+        const size_t sb = (size_t)a.nb * kbytes, se = (size_t)a.na * 4;
+        stage = sb <= 200 * 1024;
+        const size_t sbs = stage ? (sb + 15) / 16 * 16 : 0;
+        stage_e = sbs + se <= 200 * 1024;
+        return sbs + (stage_e ? se : 0);
+    };
+    u32 stage = 0, stage_e = 0;
     if (a.A32) {
-        const size_t sb = (size_t)a.nb * 4;
-        const u32 stage = sb <= 200 * 1024;
-        set_smem(k_find_edge<u32>, stage ? sb : 0);
-        k_find_edge<u32><<<fgrid, DT, stage ? sb : 0, c.s>>>(a.A32, a.B32, a.na, a.nb, W, wpos + G, a.E, a.i0s,
-                                                             a.i1s, a.cnt, stage);
+        const size_t bytes = fe_smem(4, stage, stage_e);
+        set_smem(k_find_edge<u32>, bytes);
+        k_find_edge<u32><<<fgrid, DT, bytes, c.s>>>(a.A32, a.B32, a.na, a.nb, W, wpos + G, a.E, a.i0s, a.i1s,
+                                                    a.cnt, stage, stage_e);
     } else {
-        const size_t sb = (size_t)a.nb * 8;
-        const u32 stage = sb <= 200 * 1024;
-        set_smem(k_find_edge<u64>, stage ? sb : 0);
-        k_find_edge<u64><<<fgrid, DT, stage ? sb : 0, c.s>>>(a.A, a.B, a.na, a.nb, W, wpos + G, a.E, a.i0s, a.i1s,
-                                                             a.cnt, stage);
+        const size_t bytes = fe_smem(8, stage, stage_e);
+        set_smem(k_find_edge<u64>, bytes);
+        k_find_edge<u64><<<fgrid, DT, bytes, c.s>>>(a.A, a.B, a.na, a.nb, W, wpos + G, a.E, a.i0s, a.i1s, a.cnt,
+                                                    stage, stage_e);
     }
     PM_LAUNCHED(c);
 
