@@ -122,6 +122,13 @@ typedef struct pm_options {
     uint32_t cost_window;      /* direct: cost of one window in term products
                                   (0 = 23000); the groups balance
                                   products + cost_row rows + cost_window windows    */
+    uint32_t grid_l;           /* the parameter l of the Sec. 5 almost regular grid
+                                  ((l+1)^2 points of the pp-matrix, 1..4096; 0 =
+                                  chosen from the sizes): sort, the first
+                                  splitters before counting and refinement;
+                                  direct, the cost sample of the groups.  64 is
+                                  the paper's setting.  The result does not
+                                  depend on it                                      */
 } pm_options;
 
 /* Per-call counters (all optional; pass NULL). */
@@ -236,7 +243,7 @@ void pm_plan_destroy(pm_plan *plan);
  * products of that class.  h receives the product.  pm_batch_autotune does
  * the same for a batch's range size and ranges per work item, timing plans
  * on an evenly spaced sample of at most 256 items. */
-#define PM_TUNE_MAX_CANDIDATES 16
+#define PM_TUNE_MAX_CANDIDATES 24
 
 typedef struct pm_tune_report {
     uint32_t count;            /* candidates timed                                */

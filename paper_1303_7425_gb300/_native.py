@@ -40,7 +40,7 @@ class pm_terms_out(C.Structure):
 class pm_options(C.Structure):
     _fields_ = [("strategy", C.c_int32), ("slots", C.c_uint32), ("chunk", C.c_uint32),
                 ("ranges_per_sm", C.c_uint32), ("accumulator", C.c_int32), ("cost_row", C.c_uint32),
-                ("cost_window", C.c_uint32)]
+                ("cost_window", C.c_uint32), ("grid_l", C.c_uint32)]
 
 
 class pm_stats(C.Structure):
@@ -114,7 +114,7 @@ def packing(field_bits: Sequence[int]) -> pm_packing:
 
 
 def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
-            accumulator: str = "auto", cost_row: int = 0, cost_window: int = 0) -> pm_options:
+            accumulator: str = "auto", cost_row: int = 0, cost_window: int = 0, grid_l: int = 0) -> pm_options:
     o = pm_options()
     o.strategy = STRATEGY[strategy]
     o.slots = slots
@@ -123,6 +123,7 @@ def options(strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_s
     o.accumulator = ACCUMULATOR[accumulator]
     o.cost_row = cost_row
     o.cost_window = cost_window
+    o.grid_l = grid_l
     return o
 
 
@@ -171,7 +172,8 @@ def out_bound(field_bits, f_exps, g_exps, stream=None) -> int:
 
 def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61",
             strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
-            accumulator: str = "auto", out=None, stream=None, cost_row: int = 0, cost_window: int = 0) -> Product:
+            accumulator: str = "auto", out=None, stream=None, cost_row: int = 0, cost_window: int = 0,
+            grid_l: int = 0) -> Product:
     """h = f * g on the current CUDA device.
 
     f_exps/g_exps: (n, nvars) int32/uint32 CUDA tensors; f_coefs/g_coefs: (n,)
@@ -197,7 +199,7 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
     h.coefs = coefs.data_ptr()
     h.cap = cap
     st = pm_stats()
-    o = options(strategy, slots, chunk, ranges_per_sm, accumulator, cost_row, cost_window)
+    o = options(strategy, slots, chunk, ranges_per_sm, accumulator, cost_row, cost_window, grid_l)
     rc = lib().pm_polymul(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(o),
                           C.byref(st), _stream_handle(stream))
     if rc != PM_OK:
@@ -582,7 +584,7 @@ class Server:
 # autotuner (pm_autotune, pm_batch_autotune)
 # ---------------------------------------------------------------------------
 
-PM_TUNE_MAX_CANDIDATES = 16
+PM_TUNE_MAX_CANDIDATES = 24
 
 
 class pm_tune_report(C.Structure):
@@ -598,7 +600,7 @@ class pm_batch_tune_report(C.Structure):
 def _opts_dict(o: pm_options) -> dict:
     return dict(strategy=STRATEGY_NAME.get(o.strategy, o.strategy), slots=o.slots, chunk=o.chunk,
                 ranges_per_sm=o.ranges_per_sm, accumulator={v: k for k, v in ACCUMULATOR.items()}.get(o.accumulator),
-                cost_row=o.cost_row, cost_window=o.cost_window)
+                cost_row=o.cost_row, cost_window=o.cost_window, grid_l=o.grid_l)
 
 
 def autotune(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61", stream=None):

@@ -273,7 +273,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 2)
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 2 ||
+        o.grid_l > 4096)
         throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
     memset(&stats, 0, sizeof(stats));
@@ -310,7 +311,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     Layout raw = L;
     const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
     if (!opt || (!o.strategy && !o.slots && !o.chunk && !o.ranges_per_sm && !o.accumulator && !o.cost_row &&
-                 !o.cost_window)) {
+                 !o.cost_window && !o.grid_l)) {
         // default options: use the autotuner's choice for this shape class
         const unsigned __int128 pr = (unsigned __int128)f->n * g->n;
         const u64 bound = pr < raw_box ? (u64)pr : raw_box;
@@ -469,8 +470,12 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         u64 G64 = (u64)gps * c.sm_count;
         if (G64 > end - lo) G64 = end - lo;
         const u32 Gn = (u32)G64;
+        // the Sec. 5 grid behind the cost histogram: about 4096 points per
+        // group unless set (finer grids balanced the dense and 5-variable
+        // products a few per cent better than 256 points per group)
         u32 l = 1;
-        while ((u64)(l + 1) * (l + 1) < 256ull * Gn && l < 4096) l++;
+        while ((u64)(l + 1) * (l + 1) < 4096ull * Gn && l < 4096) l++;
+        if (o.grid_l) l = o.grid_l;
         const u32 crow = o.cost_row ? o.cost_row : 3u, cwin = o.cost_window ? o.cost_window : 23000u;
         const u64 *gb = direct_groups(c, S, F.rank, (u32)F.n, G.rank, (u32)G.n, lo, end, Gn, l, products, slots,
                                       crow, cwin);
@@ -505,10 +510,15 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     } else {
         // K-b: grid splitters, counts, refinement to the chunk capacity
         PartitionPlan plan;
+        // the first splitters: the Sec. 5 grid with about four points per
+        // chunk of term products, but at most the paper's l = 64, unless
+        // set.  Finer first grids leave many ranges far below the chunk:
+        // a 20000 x 20000 sparse 5-variable product took 568 ms with l =
+        // 624 against 192 ms with 64 (the refinement splits the rest).
         double want = 4.0 * (double)products / chunk;
         u32 l = 1;
-        while ((double)(l + 1) * (l + 1) < want && l < 2048) l++;
-        plan.grid_l = l;
+        while ((double)(l + 1) * (l + 1) < want && l < 64) l++;
+        plan.grid_l = o.grid_l ? o.grid_l : l;
         plan.target = chunk;
         plan.hard_target = true;
         plan.max_rounds = 64;

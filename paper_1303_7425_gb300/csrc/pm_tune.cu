@@ -111,7 +111,7 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
     const u64 raw_box = bound;
 
     std::vector<pm_options> cand;
-    auto add = [&](int strategy, u32 slots, u32 gps, int acc, u32 chunk, u32 crow = 0, u32 cwin = 0) {
+    auto add = [&](int strategy, u32 slots, u32 gps, int acc, u32 chunk, u32 crow = 0, u32 cwin = 0, u32 grid_l = 0) {
         pm_options o;
         memset(&o, 0, sizeof(o));
         o.strategy = strategy;
@@ -121,6 +121,7 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
         o.chunk = chunk;
         o.cost_row = crow;
         o.cost_window = cwin;
+        o.grid_l = grid_l;
         cand.push_back(o);
     };
     // direct-addressed: partition count x tile x accumulator, and the
@@ -132,8 +133,13 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
         add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 6, 12000);
         add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 1, 8000);
     }
-    // sort + reduce: chunk sizes; hashed windows
+    // the Sec. 5 grid's l: the paper's 64, and a finer grid than the sizes'
+    // choice, for the direct groups and the sort splitters
+    add(PM_STRATEGY_DIRECT, 0, 1, PM_ACC_AUTO, 0, 0, 0, 64);
+    add(PM_STRATEGY_DIRECT, 0, 1, PM_ACC_AUTO, 0, 0, 0, 1024);
+    // sort + reduce: chunk sizes and grids; hashed windows
     for (u32 chunk : {2048u, 4096u}) add(PM_STRATEGY_SORT, 0, 0, PM_ACC_AUTO, chunk);
+    for (u32 gl : {64u, 512u}) add(PM_STRATEGY_SORT, 0, 0, PM_ACC_AUTO, 4096, 0, 0, gl);
     add(PM_STRATEGY_HASH, 0, 0, PM_ACC_AUTO, 0);
 
     pm_tune_report rep;

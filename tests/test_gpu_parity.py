@@ -27,7 +27,10 @@ STRATS = [
     dict(strategy="direct", slots=512),            # many ranges, ragged tails
     dict(strategy="direct", slots=1000, ranges_per_sm=64),
     dict(strategy="direct", ranges_per_sm=3, cost_row=1, cost_window=1),   # other group boundaries
+    dict(strategy="direct", grid_l=64),            # the paper's Sec. 5 grid for the group costs
     dict(strategy="sort"),
+    dict(strategy="sort", grid_l=64),              # the paper's grid as the first splitters
+    dict(strategy="sort", grid_l=1),
     dict(strategy="sort", chunk=256),              # single-monomial ranges above the chunk
     dict(strategy="sort", chunk=1000),
 ]
@@ -52,7 +55,7 @@ def test_c1_exact(opts):
 
 
 @pytest.mark.parametrize("kind", ["m61", "i64"])
-@pytest.mark.parametrize("opts", STRATS[:7], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
+@pytest.mark.parametrize("opts", STRATS[:8], ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
 def test_dense_reduced_exact(kind, opts):
     mons = polygen.monomials_total_degree(4, 10)          # 1001 monomials
     st = polygen.Stream(1234, 0)
