@@ -127,7 +127,7 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
     // direct-addressed: partition count x tile x accumulator, and the
     // group cost model's weights
     for (u32 gps : {1u, 2u, 4u})
-        for (u32 slots : {0u, 8192u}) add(PM_STRATEGY_DIRECT, slots, gps, PM_ACC_AUTO, 0);
+        for (u32 slots : {0u, 4096u, 12288u}) add(PM_STRATEGY_DIRECT, slots, gps, PM_ACC_AUTO, 0);
     add(PM_STRATEGY_DIRECT, 0, 1, PM_ACC_WIDE, 0);
     for (u32 gps : {1u, 2u}) {
         add(PM_STRATEGY_DIRECT, 0, gps, PM_ACC_AUTO, 0, 6, 12000);
