@@ -607,6 +607,7 @@ def run_ours(args):
                     "value": we.term_products / (statistics.mean(pe[0]) * 1e-3), "unit": UNIT,
                     "ms_per_step": statistics.mean(pe[0]), "n_out": pe[1], "term_products": we.term_products,
                     "workload": "f1 = (1+x+y+z+t)^40 times f1 + 1, mod 2^61-1 (plan replay)",
+                    "frac_of_probe": we.term_products / (statistics.mean(pe[0]) * 1e-3) / peak,
                     "paper_context": "Fermi GPU, FP64 coefficients: 32 s; 64 Xeon cores, integers: 16.1 s (Sec. 6)"}
             # Examples 2 and 3 (hashed windows; host reads between rounds)
             ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
@@ -630,7 +631,8 @@ def run_ours(args):
                     "value": wx.term_products / (statistics.mean(tx) * 1e-3), "unit": UNIT,
                     "ms_per_step": statistics.mean(tx), "n_out": rx.n, "term_products": wx.term_products,
                     "strategy": rx.stats["strategy"], "window_rounds": rx.stats["refine_rounds"],
-                    "workload": wx.note, "paper_context": ctx[nm]}
+                    "workload": wx.note, "paper_context": ctx[nm],
+                    "frac_of_probe": wx.term_products / (statistics.mean(tx) * 1e-3) / peak}
                 del fx, gx, outx
                 torch.cuda.empty_cache()
             c4 = bench_batched(P, torch, args.c4_count, tune=not args.no_tune)
