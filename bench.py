@@ -355,9 +355,9 @@ def e2e_plan(P, torch, w, steps, warmup):
             for s_, d_ in zip(hf + hg, df + dg):
                 d_.copy_(s_, non_blocking=True)
             plan.run()
-            n = plan.finish()
-            hk[:n].copy_(out[0][:n], non_blocking=True)
-            hc[:n].copy_(out[1][:n], non_blocking=True)
+            # the result lands in the pinned host buffers on the device side
+            # (pm_plan_finish_to_host): one host wait per step
+            n = plan.finish_to_host(hk, hc)
             b.record()
             torch.cuda.synchronize()
             d2h = n * 16

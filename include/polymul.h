@@ -227,6 +227,18 @@ int pm_plan_run(pm_plan *plan, void *stream);
  * PM_OK, PM_EPLAN (inputs no longer match: h holds no result),
  * PM_ECAPACITY (*n_out > h->cap: nothing was written) or PM_ECUDA. */
 int pm_plan_finish(pm_plan *plan, uint64_t *n_out, void *stream);
+/* Like pm_plan_finish, and the result also lands in host memory: after the
+ * last replay on `stream`, one kernel reads the result size on the device
+ * and copies that many keys (host_keys[n]) and coefficients (host_coefs,
+ * the kind's words per term) from h into page-locked host buffers of
+ * host_cap terms (cudaMallocHost / cudaHostAlloc: device-accessible), then
+ * one synchronisation.  Returns what pm_plan_finish returns, PM_ECAPACITY
+ * also when *n_out > host_cap (nothing copied), PM_EINVAL for null or not
+ * page-locked buffers.  For plans that are not captured the copy follows
+ * the plain call's result.  The point is one host synchronisation per
+ * product instead of one for the size and one for the copies. */
+int pm_plan_finish_to_host(pm_plan *plan, uint64_t *host_keys, void *host_coefs, uint64_t host_cap,
+                           uint64_t *n_out, void *stream);
 /* 1 if the plan replays a captured graph, 0 if it runs plain calls. */
 int pm_plan_captured(const pm_plan *plan);
 void pm_plan_destroy(pm_plan *plan);

@@ -69,7 +69,8 @@ SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_autotune", 
            "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_batch_workspace",
            "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_progress",
            "pm_server_state", "pm_server_destroy", "pm_polymul_noalloc",
-           "pm_plan_create", "pm_plan_run", "pm_plan_finish", "pm_plan_captured", "pm_plan_destroy",
+           "pm_plan_create", "pm_plan_run", "pm_plan_finish", "pm_plan_finish_to_host", "pm_plan_captured",
+           "pm_plan_destroy",
            "pm_strerror", "pm_version", "pm_probe_mac")
 
 _lib = None
@@ -221,6 +222,9 @@ def _plan_lib():
         L.pm_plan_run.restype = C.c_int
         L.pm_plan_finish.argtypes = [C.c_void_p, P(C.c_uint64), C.c_void_p]
         L.pm_plan_finish.restype = C.c_int
+        L.pm_plan_finish_to_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, P(C.c_uint64),
+                                             C.c_void_p]
+        L.pm_plan_finish_to_host.restype = C.c_int
         L.pm_plan_captured.argtypes = [C.c_void_p]
         L.pm_plan_captured.restype = C.c_int
         L.pm_plan_destroy.argtypes = [C.c_void_p]
@@ -271,6 +275,23 @@ class Plan:
         rc = _plan_lib().pm_plan_finish(self.handle, C.byref(n), _stream_handle(stream))
         if rc != PM_OK:
             err = PolymulError(rc, "pm_plan_finish")
+            err.needed = int(n.value)
+            raise err
+        return int(n.value)
+
+    def finish_to_host(self, host_keys, host_coefs, stream=None) -> int:
+        """finish(), with the result also copied on the device side into the
+        page-locked CPU tensors host_keys (cap,) and host_coefs (cap,) or
+        (cap, words) (torch ``pin_memory()``): one host wait per product.
+        Returns the result size."""
+        for t in (host_keys, host_coefs):
+            if t.is_cuda or not t.is_pinned() or not t.is_contiguous():
+                raise PolymulError(PM_EINVAL, "host buffers must be contiguous page-locked CPU tensors")
+        n = C.c_uint64(0)
+        rc = _plan_lib().pm_plan_finish_to_host(self.handle, host_keys.data_ptr(), host_coefs.data_ptr(),
+                                                int(host_keys.shape[0]), C.byref(n), _stream_handle(stream))
+        if rc != PM_OK:
+            err = PolymulError(rc, "pm_plan_finish_to_host")
             err.needed = int(n.value)
             raise err
         return int(n.value)

@@ -841,6 +841,73 @@ extern "C" int pm_plan_finish(pm_plan *p, uint64_t *n_out, void *stream)
     });
 }
 
+// The replay's result into device-accessible page-locked host memory: the
+// size is read on the device, so the host waits once.  Nothing is copied
+// when the replay did not produce a result (plan flag set) or it exceeds
+// the host buffers.
+__global__ void k_result_to_host(const u32 *__restrict__ flag, const u64 *__restrict__ nout,
+                                 const u64 *__restrict__ keys, const u64 *__restrict__ coefs, u32 words,
+                                 u64 *__restrict__ hkeys, u64 *__restrict__ hcoefs, u64 hcap)
+{
+    const u64 n = *nout;
+    if ((flag && *flag) || n > hcap) return;
+    const u64 stride = (u64)gridDim.x * blockDim.x;
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) hkeys[t] = keys[t];
+    for (u64 t = (u64)blockIdx.x * blockDim.x + threadIdx.x; t < n * words; t += stride) hcoefs[t] = coefs[t];
+}
+
+extern "C" int pm_plan_finish_to_host(pm_plan *p, uint64_t *host_keys, void *host_coefs, uint64_t host_cap,
+                                      uint64_t *n_out, void *stream)
+{
+    if (!p || !host_keys || !host_coefs) return PM_EINVAL;
+    return guarded([&] {
+        cudaStream_t s = (cudaStream_t)stream;
+        void *dk = nullptr, *dc = nullptr;
+        if (cudaHostGetDevicePointer(&dk, host_keys, 0) != cudaSuccess ||
+            cudaHostGetDevicePointer(&dc, host_coefs, 0) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error(PM_EINVAL, "host buffers are not page-locked and device-accessible");
+        }
+        const u32 words = p->kind == PM_COEF_M61 ? 1u : (p->kind == PM_COEF_I64_ACC192 ? 3u : 2u);
+        int sms = 0, dev = 0;
+        PM_CUDA(cudaGetDevice(&dev));
+        PM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        if (!p->captured) {
+            // the plain call already finished: its size is on the host
+            if (p->last_rc != PM_OK) {
+                if (n_out) *n_out = p->last_n;
+                return p->last_rc;
+            }
+            if (n_out) *n_out = p->last_n;
+            if (p->last_n > host_cap) return PM_ECAPACITY;
+            if (p->last_n) {
+                PM_CUDA(cudaMemcpyAsync(dk, p->h.keys, p->last_n * 8, cudaMemcpyDeviceToHost, s));
+                PM_CUDA(cudaMemcpyAsync(dc, p->h.coefs, p->last_n * 8 * words, cudaMemcpyDeviceToHost, s));
+                PM_CUDA(cudaStreamSynchronize(s));
+            }
+            return PM_OK;
+        }
+        k_result_to_host<<<sms * 4, 256, 0, s>>>(p->rec.d_flag, p->rec.d_nout, (const u64 *)p->h.keys,
+                                                 (const u64 *)p->h.coefs, words, (u64 *)dk, (u64 *)dc, host_cap);
+        PM_CUDA(cudaGetLastError());
+        PM_CUDA(cudaMemcpyAsync(p->host, p->rec.d_flag, 4, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaMemcpyAsync(p->host + 1, &p->rec.d_small->status, 4, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaMemcpyAsync(p->host + 2, p->rec.d_nout, 8, cudaMemcpyDeviceToHost, s));
+        PM_CUDA(cudaStreamSynchronize(s));
+        const u32 flag = p->host[0], status = p->host[1];
+        u64 n = 0;
+        memcpy(&n, p->host + 2, 8);
+        if (flag & PLAN_MISMATCH) {
+            if (n_out) *n_out = 0;
+            return PM_EPLAN;
+        }
+        if (status & ST_INTERNAL) throw Error(PM_ECUDA, "internal consistency check failed");
+        if (n_out) *n_out = n;
+        if (flag & PLAN_CAPACITY) return PM_ECAPACITY;
+        return n > host_cap ? PM_ECAPACITY : PM_OK;
+    });
+}
+
 extern "C" int pm_plan_captured(const pm_plan *p) { return p && p->captured ? 1 : 0; }
 
 extern "C" void pm_plan_destroy(pm_plan *p) { plan_free(p); }

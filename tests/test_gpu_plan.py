@@ -187,3 +187,55 @@ def test_plan_sort_strategy_runs_plain_calls():
         _expect(w, plan.finish(), out)
     finally:
         plan.close()
+
+
+@pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_plan_finish_to_host_equals_device_result(kind):
+    """The replay's result copied on the device side into page-locked host
+    buffers equals the device result; the host waits once."""
+    import torch
+    import paper_1303_7425_gb300 as P
+    w = _dense(kind=kind, seed=13)
+    f, g, out = _make(w)
+    plan = P.Plan(w.field_bits, f[0], f[1], g[0], g[1], out, kind=kind)
+    try:
+        cap = out[0].shape[0]
+        hk = torch.full((cap,), -1, dtype=torch.int64).pin_memory()
+        hc = torch.full(tuple(out[1].shape), -1, dtype=torch.int64).pin_memory()
+        for _ in range(2):
+            plan.run()
+            n = plan.finish_to_host(hk, hc)
+            _expect(w, n, out)
+            assert torch.equal(hk[:n], out[0][:n].cpu()) and torch.equal(hc[:n], out[1][:n].cpu())
+        # a host buffer smaller than the result: nothing copied, size reported
+        small_k = torch.full((n - 1,), -5, dtype=torch.int64).pin_memory()
+        small_c = torch.full((n - 1,) + tuple(out[1].shape[1:]), -5, dtype=torch.int64).pin_memory()
+        plan.run()
+        with pytest.raises(P.PolymulError) as ei:
+            plan.finish_to_host(small_k, small_c)
+        assert ei.value.code == -4 and ei.value.needed == n
+        assert bool((small_k == -5).all())
+        # pageable host memory is refused
+        with pytest.raises(P.PolymulError) as ei:
+            plan.finish_to_host(torch.empty(cap, dtype=torch.int64), hc)
+        assert ei.value.code == -1
+    finally:
+        plan.close()
+
+
+def test_plan_finish_to_host_sort_strategy_plain_calls():
+    import torch
+    import paper_1303_7425_gb300 as P
+    w = polygen.sparse_product(polygen.Stream(43, 0), 5, 200, 150)
+    f, g, out = _make(w)
+    plan = P.Plan(w.field_bits, f[0], f[1], g[0], g[1], out)
+    try:
+        assert not plan.captured
+        hk = torch.empty(out[0].shape[0], dtype=torch.int64).pin_memory()
+        hc = torch.empty(out[1].shape[0], dtype=torch.int64).pin_memory()
+        plan.run()
+        n = plan.finish_to_host(hk, hc)
+        _expect(w, n, out)
+        assert torch.equal(hk[:n], out[0][:n].cpu()) and torch.equal(hc[:n], out[1][:n].cpu())
+    finally:
+        plan.close()
