@@ -59,10 +59,10 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4"],
-                    help="what the timed steps run (profiling); the reported line is for c2")
-    ap.add_argument("--c4-count", type=int, default=4096, help="products of the batched workload")
-    ap.add_argument("--c5-count", type=int, default=3000, help="requests of the serving workload")
+    ap.add_argument("--workload", default="dense4v", choices=["dense4v", "sparse5v", "batch"],
+                    help="what the timed steps run (profiling); the reported line is for dense4v")
+    ap.add_argument("--batch-count", type=int, default=4096, help="products of the batched workload")
+    ap.add_argument("--serving-count", type=int, default=3000, help="requests of the serving workload")
     return ap.parse_args()
 
 
@@ -100,7 +100,7 @@ def run_reference(args):
         return
     import oracle
     import polygen
-    w = polygen.workload_c2()
+    w = polygen.workload_dense4v()
     rows = 1000                                   # bounded sample: 1000 rows of f x all of g
     fe, fc = w.f.exps[:rows], w.f.coefs[:rows]
     prods = rows * w.g.n
@@ -389,13 +389,13 @@ def _device_product(torch, np, w, cap=None):
 
 
 def bench_batched(P, torch, count, tune=True):
-    """c4: `count` independent sparse products -- one captured batched pass
+    """The batched workload: `count` independent sparse products -- one captured batched pass
     versus one pm_polymul launch per product, on the same GPU."""
     import numpy as np
 
     import oracle
     import polygen
-    ws = polygen.workload_c4(count)
+    ws = polygen.workload_sparse_batch(count)
     prods = [_device_product(torch, np, w) for w in ws]
     tp = sum(w.term_products for w in ws)
     best = P.batch_autotune(prods)[0] if tune else {}
@@ -456,14 +456,14 @@ def bench_batched(P, torch, count, tune=True):
 
 
 def bench_serving(P, torch, count, rate_hz, tune=True):
-    """c5: Poisson arrivals at `rate_hz`, 95% c4-distribution and 5% dense
-    c2-shape products, continuous batching under a 64 GiB HBM budget."""
+    """Serving: Poisson arrivals at `rate_hz`, 95% batch-distribution and 5%
+    dense 4-variable products, continuous batching under a 64 GiB HBM budget."""
     import numpy as np
 
     import oracle
     import polygen
     from paper_1303_7425_gb300.serving import serve
-    reqs = polygen.workload_c5(rate_hz, count)
+    reqs = polygen.workload_serving_mix(rate_hz, count)
     prods = [_device_product(torch, np, r.work, cap=(200_000 if r.dense else None)) for r in reqs]
     rep = serve([(r.t_arrival, pr) for r, pr in zip(reqs, prods)], [r.work.term_products for r in reqs],
                 server_kwargs=dict(device_budget=64 << 30, streams=4, max_batch=256))
@@ -534,11 +534,12 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.lib()  # fails loudly if the CUDA library is missing
 
-    w = {"c2": polygen.workload_c2, "c3": polygen.workload_c3}.get(args.workload, polygen.workload_c2)()
+    w = {"dense4v": polygen.workload_dense4v, "sparse5v": polygen.workload_sparse5v}.get(
+        args.workload, polygen.workload_dense4v)()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     products = w.term_products
-    if args.workload == "c4":  # profiling aid: the batched pass as the timed step
-        print(json.dumps(bench_batched(P, torch, args.c4_count, tune=not args.no_tune)))
+    if args.workload == "batch":  # profiling aid: the batched pass as the timed step
+        print(json.dumps(bench_batched(P, torch, args.batch_count, tune=not args.no_tune)))
         return
     tuned = None
     if not args.no_tune:
@@ -576,7 +577,7 @@ def run_ours(args):
         achieved = products / (kern_ms * 1e-3)
         kname = "k_direct" if stats[-1]["strategy"] == "direct" else "k_range_sort"
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                "traffic": traffic_for(kname, "c2_m61" if args.workload == "c2" else args.workload),
+                "traffic": traffic_for(kname, "dense4v_m61" if args.workload == "dense4v" else args.workload),
                 "kernel": kname,
                 "range_step_ms": statistics.mean(s["ms_range_step"] for s in stats),
                 "kernel_ms": kern_ms, "kernel_share_of_step": kern_ms / ms_step,
@@ -588,25 +589,25 @@ def run_ours(args):
         else:
             e2e_ms, h2d, d2h = e2e_product(P, torch, w, max(5, min(args.steps, 50)), 3)
         e2e_val = products / (statistics.mean(e2e_ms) * 1e-3)
-        extras = {"c2_plain_call": {"value": products / (statistics.mean(ms_plain) * 1e-3), "unit": UNIT,
+        extras = {"dense4v_plain_call": {"value": products / (statistics.mean(ms_plain) * 1e-3), "unit": UNIT,
                                     "ms_per_step": statistics.mean(ms_plain),
                                     "host_syncs_per_step": stats[-1]["host_syncs"],
                                     "api": "pm_polymul (host reads sizes between steps)"}}
         # the secondary workloads run on one GPU only (with N ranks the
         # others would wait for rank 0 at the closing barrier)
         if not args.no_extras and world == 1:
-            wi = polygen.workload_c2("i64")
+            wi = polygen.workload_dense4v("i64")
             ms_i, st_i, _ = time_product(P, torch, wi, 20, 3, flush, kind="i64")
-            extras["c2_int64_acc128"] = {"value": wi.term_products / (statistics.mean(ms_i) * 1e-3), "unit": UNIT,
+            extras["dense4v_int64_acc128"] = {"value": wi.term_products / (statistics.mean(ms_i) * 1e-3), "unit": UNIT,
                                          "ms_per_step": statistics.mean(ms_i),
                                          "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_i)}
-            w3 = polygen.workload_c3()
+            w3 = polygen.workload_sparse5v()
             if not args.no_tune:
                 f3 = _dev(torch, np, w3.f)
                 g3 = _dev(torch, np, w3.g)
                 P.autotune(w3.field_bits, f3[0], f3[1], g3[0], g3[1])
             ms_3, st_3, r3 = time_product(P, torch, w3, 5, 2, flush)
-            extras["c3_sparse5v_50000x50000"] = {
+            extras["sparse5v_50000x50000"] = {
                 "value": w3.term_products / (statistics.mean(ms_3) * 1e-3), "unit": UNIT,
                 "ms_per_step": statistics.mean(ms_3), "n_out": r3.n,
                 "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_3),
@@ -647,14 +648,14 @@ def run_ours(args):
                     "frac_of_probe": wx.term_products / (statistics.mean(tx) * 1e-3) / peak}
                 del fx, gx, outx
                 torch.cuda.empty_cache()
-            c4 = bench_batched(P, torch, args.c4_count, tune=not args.no_tune)
-            extras["c4_batched"] = c4
+            sb = bench_batched(P, torch, args.batch_count, tune=not args.no_tune)
+            extras["sparse_batch_4096"] = sb
             # serving at ~70% of the measured capacity for the request mix:
             # 95% sparse requests at the batched pass's time per product, 5%
             # dense ones at the dense step's time
-            t_req = 0.95 * c4["batched_ms"] * 1e-3 / args.c4_count + 0.05 * ms_step * 1e-3
+            t_req = 0.95 * sb["batched_ms"] * 1e-3 / args.batch_count + 0.05 * ms_step * 1e-3
             rate = 0.7 / t_req
-            extras["c5_serving"] = bench_serving(P, torch, args.c5_count, rate, tune=not args.no_tune)
+            extras["serving_mix"] = bench_serving(P, torch, args.serving_count, rate, tune=not args.no_tune)
         cpu = None if (args.no_cpu or world > 1) else cpu_baseline(w)
         if cpu is not None:
             extras["cpu_alg1_threads"] = cpu_alg1(w)
@@ -662,7 +663,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 mod 2^61-1", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "c2" else args.workload,
+            "config": {"workload": WORKLOAD if args.workload == "dense4v" else args.workload,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "api": ("pm_plan_run: the whole device path as one CUDA graph, every kernel re-run "
                                "on the resident inputs each step" if planned else "pm_polymul"),

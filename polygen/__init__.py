@@ -15,11 +15,16 @@ Workload shapes follow the sparse distributed format of Sec. 2 (a list of
 (coefficient, exponent vector) terms) and the five workloads the library is
 measured on:
 
-  c1  4 variables, 1000 + 1000 distinct terms of total degree <= 12
-  c2  4 variables, all 10,626 monomials of total degree <= 20 on both sides
-  c3  5 variables, 50,000 + 50,000 distinct terms, degree caps (6,8,10,12,16)
-  c4  4096 independent products, 3..8 variables, log-uniform sizes [16,4096]
-  c5  a Poisson request stream mixing c4-shaped and c2-shaped products
+  workload_sparse4v      4 variables, 1000 + 1000 distinct terms of total
+                         degree <= 12
+  workload_dense4v       4 variables, all 10,626 monomials of total degree
+                         <= 20 on both sides
+  workload_sparse5v      5 variables, 50,000 + 50,000 distinct terms, degree
+                         caps (6,8,10,12,16)
+  workload_sparse_batch  4096 independent products, 3..8 variables,
+                         log-uniform sizes [16,4096]
+  workload_serving_mix   a Poisson request stream mixing batch-shaped and
+                         dense 4-variable products
 """
 
 from __future__ import annotations
@@ -174,7 +179,7 @@ def _poly(st: Stream, exps: np.ndarray, kind: str, i64_bound: int = 1 << 20) -> 
     return Poly(exps, c)
 
 
-def workload_c1(seed: Optional[int] = None) -> Workload:
+def workload_sparse4v(seed: Optional[int] = None) -> Workload:
     seed = BASE_SEED + 0 if seed is None else seed
     mons = monomials_total_degree(4, 12)                 # 1820 monomials
     out = []
@@ -182,18 +187,18 @@ def workload_c1(seed: Optional[int] = None) -> Workload:
         st = Stream(seed, sid)
         pick = st.permutation(mons.shape[0])[:1000]
         out.append(_poly(st, mons[pick], "m61"))
-    return Workload("c1_sparse4v_1000x1000_m61", 4, [16] * 4, "m61", out[0], out[1],
+    return Workload("sparse4v_1000x1000_m61", 4, [16] * 4, "m61", out[0], out[1],
                     "4 vars, 16-bit fields, 1000 distinct terms of degree <= 12 per operand")
 
 
-def workload_c2(kind: str = "m61", seed: Optional[int] = None) -> Workload:
+def workload_dense4v(kind: str = "m61", seed: Optional[int] = None) -> Workload:
     seed = BASE_SEED + 1 if seed is None else seed
     mons = monomials_total_degree(4, 20)                 # 10626 monomials
     out = []
     for sid in (0, 1):
         st = Stream(seed, sid + (2 if kind == "i64" else 0))
         out.append(_poly(st, mons, kind))
-    return Workload(f"c2_dense4v_deg20_{kind}", 4, [16] * 4, kind, out[0], out[1],
+    return Workload(f"dense4v_deg20_{kind}", 4, [16] * 4, kind, out[0], out[1],
                     "4 vars, all 10626 monomials of degree <= 20 on both sides")
 
 
@@ -241,7 +246,7 @@ def paper_example(name: str) -> Workload:
 C3_CAPS = (6, 8, 10, 12, 16)
 
 
-def workload_c3(seed: Optional[int] = None, n: int = 50000) -> Workload:
+def workload_sparse5v(seed: Optional[int] = None, n: int = 50000) -> Workload:
     seed = BASE_SEED + 2 if seed is None else seed
     pts = box_points(C3_CAPS)                            # 153153 points
     out = []
@@ -249,7 +254,7 @@ def workload_c3(seed: Optional[int] = None, n: int = 50000) -> Workload:
         st = Stream(seed, sid)
         pick = st.permutation(pts.shape[0])[:n]
         out.append(_poly(st, pts[pick], "m61"))
-    return Workload(f"c3_sparse5v_{n}x{n}_m61", 5, [12] * 5, "m61", out[0], out[1],
+    return Workload(f"sparse5v_{n}x{n}_m61", 5, [12] * 5, "m61", out[0], out[1],
                     "5 vars, degree caps (6,8,10,12,16), 12-bit fields")
 
 
@@ -270,7 +275,7 @@ def sparse_product(st: Stream, nvars: int, nf: int, ng: int, exp_hi: Optional[in
     return Workload(f"sparse{nvars}v_{nf}x{ng}", nvars, bits, "m61", f, g)
 
 
-def workload_c4(count: int = 4096, seed: Optional[int] = None,
+def workload_sparse_batch(count: int = 4096, seed: Optional[int] = None,
                 exp_hi: Optional[int] = None) -> List[Workload]:
     """The batched workload: ``count`` independent sparse products."""
     seed = BASE_SEED + 3 if seed is None else seed
@@ -292,9 +297,10 @@ class Request:
     dense: bool
 
 
-def workload_c5(rate_hz: float, count: int, seed: Optional[int] = None,
+def workload_serving_mix(rate_hz: float, count: int, seed: Optional[int] = None,
                 dense_frac: float = 0.05) -> List[Request]:
-    """Poisson arrivals; 95% c4-distribution products, 5% c2-shape dense ones."""
+    """Poisson arrivals; 95% products drawn like workload_sparse_batch's, 5%
+    dense 4-variable ones of workload_dense4v's shape."""
     seed = BASE_SEED + 4 if seed is None else seed
     st = Stream(seed, 0)
     gaps = -np.log(1.0 - st.uniform01(count)) / rate_hz

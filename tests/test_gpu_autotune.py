@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 def test_autotune_then_default_call_uses_it():
     import paper_1303_7425_gb300 as P
-    w = polygen.workload_c1()
+    w = polygen.workload_sparse4v()
     f = to_dev(w.f.exps, w.f.coefs)
     g = to_dev(w.g.exps, w.g.coefs)
     best, table = P.autotune(w.field_bits, f[0], f[1], g[0], g[1])

@@ -45,8 +45,8 @@ def _oracle(w, fe=None, fc=None, ge=None, gc=None):
 
 
 @pytest.mark.parametrize("opts", STRATS, ids=lambda o: "-".join(f"{k}{v}" for k, v in o.items()))
-def test_c1_exact(opts):
-    w = polygen.workload_c1()
+def test_sparse4v_exact(opts):
+    w = polygen.workload_sparse4v()
     ref = _oracle(w)
     gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, **opts)
     check_canonical(gpu[0], gpu[1], w.field_bits)
@@ -92,10 +92,10 @@ def _sampled_check(w, gpu, nsample=120, seed=0):
 
 @pytest.mark.parametrize("kind", ["m61", "i64"])
 @pytest.mark.parametrize("acc", ["auto", "wide"])
-def test_c2_full_size(kind, acc):
+def test_dense4v_full_size(kind, acc):
     """The dense workload at full size: 10626 x 10626 terms, exactly
     C(44, 4) = 135751 result terms, sampled coefficients, evaluation."""
-    w = polygen.workload_c2(kind)
+    w = polygen.workload_dense4v(kind)
     gpu = run_gpu(w.field_bits, kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, accumulator=acc)
     check_canonical(gpu[0], gpu[1], w.field_bits, kind)
     assert gpu[0].shape[0] == math.comb(44, 4)
@@ -127,8 +127,8 @@ def test_direct_every_row_has_products(nf, ng, slots, kind):
     assert_same(gpu, _oracle(w), w.field_bits)
 
 
-def test_c3_reduced_exact():
-    w = polygen.workload_c3(n=3000)
+def test_sparse5v_reduced_exact():
+    w = polygen.workload_sparse5v(n=3000)
     ref = _oracle(w)
     for opts in (dict(strategy="auto"), dict(strategy="sort"), dict(strategy="direct", slots=4096),
                  dict(strategy="direct", accumulator="wide")):
@@ -136,9 +136,9 @@ def test_c3_reduced_exact():
         assert_same(gpu, ref, w.field_bits)
 
 
-def test_c3_full_size():
+def test_sparse5v_full_size():
     """The sparse five-variable workload at full size (2.5e9 term products)."""
-    w = polygen.workload_c3()
+    w = polygen.workload_sparse5v()
     gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
     keys = gpu[0]
     check_canonical(keys, gpu[1], w.field_bits)
@@ -177,7 +177,7 @@ def test_sparse_heavy_collisions():
 
 
 def test_commutative_bit_exact():
-    w = polygen.workload_c1()
+    w = polygen.workload_sparse4v()
     a = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
     b = run_gpu(w.field_bits, "m61", w.g.exps, w.g.coefs, w.f.exps, w.f.coefs)
     np.testing.assert_array_equal(a[0], b[0])
@@ -258,12 +258,12 @@ def test_direct_rank_decoding_extents(bits, lims):
     assert_same(gpu, ref, bits)
 
 
-@pytest.mark.parametrize("case", ["c1", "dense_i64", "sparse3", "sparse5", "collisions"])
+@pytest.mark.parametrize("case", ["sparse4v", "dense_i64", "sparse3", "sparse5", "collisions"])
 def test_hash_strategy_exact(case):
     """Hashed windows (PM_STRATEGY_HASH) on dense, sparse and colliding
     products, both coefficient kinds: bit-exact with the oracle."""
-    if case == "c1":
-        w = polygen.workload_c1()
+    if case == "sparse4v":
+        w = polygen.workload_sparse4v()
     elif case == "dense_i64":
         mons = polygen.monomials_total_degree(3, 10)
         st = polygen.Stream(5, 1)
@@ -369,7 +369,7 @@ def test_capacity_error_reports_needed_size():
     import paper_1303_7425_gb300 as P
     import torch
     from tests.gpu_util import to_dev
-    w = polygen.workload_c1()
+    w = polygen.workload_sparse4v()
     f = to_dev(w.f.exps, w.f.coefs)
     g = to_dev(w.g.exps, w.g.coefs)
     out = (torch.empty(10, dtype=torch.int64, device="cuda"), torch.empty(10, dtype=torch.int64, device="cuda"))

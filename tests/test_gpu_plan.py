@@ -68,7 +68,7 @@ def test_plan_replays_equal_oracle(kind):
 def test_plan_dense_workload_equals_plain_call():
     """The 10,626 x 10,626 dense product: replays equal pm_polymul."""
     import paper_1303_7425_gb300 as P
-    w = polygen.workload_c2()
+    w = polygen.workload_dense4v()
     f, g, out = _make(w, cap=200_000)
     plan = P.Plan(w.field_bits, f[0], f[1], g[0], g[1], out)
     try:

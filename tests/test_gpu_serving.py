@@ -33,7 +33,7 @@ def _stream(count=150, dense=3, seed=17, rate=20000.0, hi=800):
     ws = [polygen.sparse_product(polygen.Stream(seed, 10 + k), int(nv[k]), int(nf[k]), int(ng[k]))
           for k in range(count)]
     for k in range(dense):
-        ws.insert(10 + 40 * k, polygen.workload_c2(seed=seed + k))
+        ws.insert(10 + 40 * k, polygen.workload_dense4v(seed=seed + k))
     gaps = -np.log(1.0 - st.uniform01(len(ws))) / rate
     return ws, np.cumsum(gaps)
 

@@ -346,7 +346,7 @@ def test_grid_matches_hand_derived_fixture():
 
 @pytest.mark.parametrize("l,threads", [(1, 1), (2, 3), (8, 4), (64, 2)])
 def test_alg1_equals_definition(l, threads):
-    w = polygen.workload_c1()
+    w = polygen.workload_sparse4v()
     ref = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps[:300], w.f.coefs[:300],
                      w.g.exps[:250], w.g.coefs[:250])
     e, c, ni = oracle.mul_alg1(w.nvars, w.field_bits, "m61", w.f.exps[:300], w.f.coefs[:300],
