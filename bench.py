@@ -1,13 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the exact sparse polynomial product on GB300.
 
-One step = one pm_polymul call (pack + partition + range kernel + compaction)
-on the dense four-variable workload: f and g each hold all 10,626 monomials
-of total degree <= 20 with seeded coefficients mod 2^61-1 (112,911,876 term
-products collapsing to 135,751 result terms).  Inputs are resident in HBM;
-L2 is flushed (256 MiB write) between timed steps, outside the step's events.
+One step = one whole product h = f * g (pack + partition + FindEdge + range
+kernel + compaction), replayed as one captured CUDA graph (pm_plan_run) on
+the largest single-GPU workload: the sparse five-variable product, f and g
+each 50,000 distinct terms of the box with degree caps (6, 8, 10, 12, 16),
+coefficients mod 2^61-1 (2.5e9 term products collapsing to 3,824,065 result
+terms).  Inputs are resident in HBM; L2 is flushed (256 MiB write) between
+timed steps, outside the step's events.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload sparse5v|dense4v|sparse4v|batch]
 
 Under torchrun (N > 1) every rank runs its own replica of the product on its
 own GPU (independent products, no collective on the data path); value is the
@@ -36,9 +39,30 @@ sys.path.insert(0, ROOT)
 
 METRIC = "exact term products/sec (1 GB300, % roofline); batched vs plain speedup; p99 ms"
 UNIT = "term products/s"
-WORKLOAD = ("dense 4-variable product: f, g = all 10,626 monomials of total degree <= 20, "
-            "coefficients mod 2^61-1, 16-bit fields (112,911,876 term products -> 135,751 terms)")
+WORKLOADS = {
+    "sparse5v": ("sparse 5-variable product: f, g = 50,000 distinct terms each of the box with degree caps "
+                 "(6,8,10,12,16), coefficients mod 2^61-1, 12-bit fields (2.5e9 term products -> 3,824,065 terms)"),
+    "dense4v": ("dense 4-variable product: f, g = all 10,626 monomials of total degree <= 20, "
+                "coefficients mod 2^61-1, 16-bit fields (112,911,876 term products -> 135,751 terms)"),
+    "sparse4v": ("sparse 4-variable product: f, g = 1000 distinct terms each of total degree <= 12, "
+                 "coefficients mod 2^61-1, 16-bit fields (1e6 term products)"),
+}
+# the oracle's bounded samples: rows of f times all of g
+CPU_ROWS = {"sparse5v": 1000, "dense4v": 10626, "sparse4v": 1000}
+REF_ROWS = {"sparse5v": 200, "dense4v": 1000, "sparse4v": 1000}
 FLUSH_BYTES = 256 << 20
+# Sec. 8(d)'s algorithmic operation count of one term product in the split
+# multiply form: four 32 x 32 -> 64 multiplies; about fourteen simple ops
+# (key add, guard test, the adds of the partial products, the Mersenne fold,
+# one modular add)
+OPS_WIDE, OPS_SIMPLE = 4, 14
+ISSUE_LANES_PER_CLK = 128     # 4 schedulers per SM, one 32-lane warp instruction each per clock
+
+
+def _workload(name):
+    import polygen
+    return {"sparse5v": polygen.workload_sparse5v, "dense4v": polygen.workload_dense4v,
+            "sparse4v": polygen.workload_sparse4v}[name]()
 
 
 def hbm_peak():
@@ -59,8 +83,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
-    ap.add_argument("--workload", default="dense4v", choices=["dense4v", "sparse5v", "batch"],
-                    help="what the timed steps run (profiling); the reported line is for dense4v")
+    ap.add_argument("--workload", default="sparse5v", choices=["sparse5v", "dense4v", "sparse4v", "batch"],
+                    help="what the timed steps run; the line reports that workload (default: the largest)")
     ap.add_argument("--batch-count", type=int, default=4096, help="products of the batched workload")
     ap.add_argument("--serving-count", type=int, default=3000, help="requests of the serving workload")
     return ap.parse_args()
@@ -99,9 +123,9 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    import polygen
-    w = polygen.workload_dense4v()
-    rows = 1000                                   # bounded sample: 1000 rows of f x all of g
+    name = args.workload if args.workload in WORKLOADS else "sparse5v"
+    w = _workload(name)
+    rows = min(REF_ROWS[name], w.f.n)             # bounded sample: rows of f x all of g
     fe, fc = w.f.exps[:rows], w.f.coefs[:rows]
     prods = rows * w.g.n
     for _ in range(args.warmup):
@@ -118,7 +142,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64 mod 2^61-1", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": sample},
+        "config": {"workload": WORKLOADS[name], "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
@@ -210,7 +234,8 @@ def time_product(P, torch, w, steps, warmup, flush, kind="m61", stream=None):
 
 
 def probe_peak(P, torch):
-    """Measured rate of the per-term-product arithmetic (register-only)."""
+    """Measured rate of the per-term-product arithmetic loop (register-only,
+    pm_probe_mac; it also carries one operand-advance add and mask)."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks, threads, iters = sms * 8, 256, 1 << 14
     sink = torch.empty(blocks * threads, dtype=torch.int64, device="cuda")
@@ -226,6 +251,59 @@ def probe_peak(P, torch):
         torch.cuda.synchronize()
         best = max(best, blocks * threads * 4 * iters / (a.elapsed_time(b) * 1e-3))
     return best
+
+
+def oprate_peak(P, torch):
+    """The integer-op bound of one term product, derived from measured
+    instruction rates (register-only probes, pm_probe_oprate): per SM and
+    clock, r_wide 32x32->64 multiply-adds, r_simple simple ops (the fastest
+    of three-input add, three-input logic op and funnel shift) and the issue
+    limit of 128 lane-instructions.  A term product needs OPS_WIDE wide
+    multiplies and OPS_SIMPLE simple ops, so an SM needs at least
+    max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple, (OPS_WIDE + OPS_SIMPLE) / 128)
+    clocks per product.  The bound is SMs x clock / that; the measured rate
+    of the same 4:14 mix on independent chains is reported beside it, and
+    the larger of the two is the peak."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    blocks, threads = sms * 4, 256
+    sink = torch.empty(blocks * threads, dtype=torch.int64, device="cuda")
+    clk = torch.zeros(2, dtype=torch.int64, device="cuda")
+    rates, mhz = {}, []
+    for op in ("imad_wide", "imad", "iadd3", "lop3", "shf", "mix"):
+        iters = (1 << 15) if op == "mix" else (1 << 16)
+        P.probe_oprate(op, blocks, threads, iters >> 4, sink, clk)      # warm-up
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            per_step = P.probe_oprate(op, blocks, threads, iters, sink, clk)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            cyc, ns = (int(x) for x in clk.cpu().tolist())
+            f_ghz = cyc / ns if ns > 0 else float("nan")
+            ops = blocks * threads * iters * per_step
+            per_sm_clk = ops / (ms * 1e-3) / (sms * f_ghz * 1e9)
+            if best is None or per_sm_clk > best[0]:
+                best = (per_sm_clk, ops / (ms * 1e-3), f_ghz * 1e3)
+        rates[op] = {"per_sm_per_clk": best[0], "lane_ops_per_s": best[1], "sm_mhz": best[2]}
+        mhz.append(best[2])
+    r_wide = rates["imad_wide"]["per_sm_per_clk"]
+    r_simple = max(rates[k]["per_sm_per_clk"] for k in ("iadd3", "lop3", "shf"))
+    # the measured mix decides whether the classes overlap: on this GPU it
+    # runs at the sum of the per-class times (one shared integer pipe), so
+    # the bound adds them; the overlapped bound (each class on a pipe of its
+    # own, issue-limited) is reported beside it
+    clk_add = OPS_WIDE / r_wide + OPS_SIMPLE / r_simple
+    clk_overlap = max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple, (OPS_WIDE + OPS_SIMPLE) / ISSUE_LANES_PER_CLK)
+    f_mhz = statistics.median(mhz)
+    model = sms * f_mhz * 1e6 / clk_add
+    mix = rates["mix"]["lane_ops_per_s"] / (OPS_WIDE + OPS_SIMPLE)
+    return {"peak": max(model, mix), "model": model, "mix_measured": mix, "clk_per_product_per_sm": clk_add,
+            "overlap_bound": sms * f_mhz * 1e6 / clk_overlap,
+            "sm_mhz": f_mhz, "sms": sms, "ops_per_product": {"wide_multiply": OPS_WIDE, "simple": OPS_SIMPLE},
+            "rates": {k: round(v["per_sm_per_clk"], 2) for k, v in rates.items()}}
 
 
 def kernel_source_hash(source: str, region=None):
@@ -498,25 +576,45 @@ def bench_serving(P, torch, count, rate_hz, tune=True):
             "hbm_budget_gib": 64}
 
 
-def cpu_baseline(w):
+def cpu_baseline(w, rows):
+    """The oracle (single thread, as it stands) on a bounded sample: the
+    first `rows` terms of f times all of g."""
     import oracle
+    rows = min(rows, w.f.n)
     t0 = time.perf_counter()
-    he, hc = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps[:rows], w.f.coefs[:rows], w.g.exps, w.g.coefs)
     dt = time.perf_counter() - t0
-    return {"value": w.term_products / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"the full workload once ({w.term_products} term products, {dt:.1f} s, single thread)",
-            "n_out": int(len(he))}
+    return {"value": rows * w.g.n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} terms of f x all {w.g.n} terms of g ({rows * w.g.n} term products, "
+                      f"{dt:.1f} s, single thread)"}
 
 
-def cpu_alg1(w, rows=2000):
+def cpu_alg1(w, rows):
     import oracle
     threads = os.cpu_count() or 1
+    rows = min(rows, w.f.n)
     t0 = time.perf_counter()
     oracle.mul_alg1(w.nvars, w.field_bits, "m61", w.f.exps[:rows], w.f.coefs[:rows], w.g.exps, w.g.coefs,
                     l=64, threads=threads)
     dt = time.perf_counter() - t0
     return {"value": rows * w.g.n / dt, "unit": UNIT, "cores": threads, "kind": "paper Alg. 1 on CPU threads",
-            "sample": f"first {rows} terms of f x all of g"}
+            "sample": f"first {rows} terms of f x all of g ({dt:.1f} s)"}
+
+
+def kernel_roofline(products, kern_ms, step_ms, kname, traffic_key, op, probe, range_step_ms):
+    achieved = products / (kern_ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved, "peak": op["peak"], "unit": UNIT, "frac": achieved / op["peak"],
+            "traffic": traffic_for(kname, traffic_key), "kernel": kname,
+            "kernel_ms": kern_ms, "range_step_ms": range_step_ms, "kernel_share_of_step": kern_ms / step_ms,
+            "peak_source": ("derived from instruction rates measured on this GPU in this run (register-only "
+                            "probes): %d wide multiplies + %d simple ops per term product at %.1f / %.1f lane-ops "
+                            "per SM per clock (wide / simple), times added (the measured 4:14 mix runs at the sum: "
+                            "%.3g products/s), %d SMs at %.0f MHz; if the classes overlapped the bound would be "
+                            "%.3g" % (OPS_WIDE, OPS_SIMPLE, op["rates"]["imad_wide"],
+                                      max(op["rates"][k] for k in ("iadd3", "lop3", "shf")), op["mix_measured"],
+                                      op["sms"], op["sm_mhz"], op["overlap_bound"])),
+            "frac_of_overlap_bound": achieved / op["overlap_bound"],
+            "frac_of_mac_probe": achieved / probe, "mac_probe": probe}
 
 
 def run_ours(args):
@@ -534,18 +632,19 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.lib()  # fails loudly if the CUDA library is missing
 
-    w = {"dense4v": polygen.workload_dense4v, "sparse5v": polygen.workload_sparse5v}.get(
-        args.workload, polygen.workload_dense4v)()
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    products = w.term_products
     if args.workload == "batch":  # profiling aid: the batched pass as the timed step
         print(json.dumps(bench_batched(P, torch, args.batch_count, tune=not args.no_tune)))
         return
+    name = args.workload
+    w = _workload(name)
+    products = w.term_products
     tuned = None
     if not args.no_tune:
         f = _dev(torch, np, w.f)
         g = _dev(torch, np, w.g)
         tuned = P.autotune(w.field_bits, f[0], f[1], g[0], g[1])[0]
+        del f, g
 
     # warm-up (also fills the stream-ordered allocator's pool)
     time_product(P, torch, w, 1, args.warmup, flush)
@@ -554,10 +653,11 @@ def run_ours(args):
     sampler = ClockSampler(local)
     torch.cuda.synchronize()
     t0 = time.time()
-    ms_plain, stats, r = time_product(P, torch, w, args.steps, 0, flush)
     # the same product as a captured plan: one CUDA graph per step, every
     # kernel re-run on the resident inputs, no host synchronisation inside
     planned = time_plan(P, torch, w, args.steps, args.warmup, flush)
+    # plain calls: the accumulate kernel timed alone with events on its stream
+    ms_plain, stats, r = time_product(P, torch, w, max(3, min(args.steps, 10)), 0, flush)
     torch.cuda.synchronize()
     t1 = time.time()
     if dist:
@@ -568,120 +668,137 @@ def run_ours(args):
     ms_step = max_over_ranks(statistics.mean(ms), dist, "cuda")
     value = whole_job_value(products, world, ms_step)
     kern_ms = statistics.mean(s["ms_range_kernel"] for s in stats)
-    # kernels per step: the call's launches (+ the plan's two check kernels)
-    launches = sum(s["kernel_launches"] + (2 if planned else 0) for s in stats)
+    # kernels per timed step: the call's launches (+ the plan's two check kernels)
+    launches = args.steps * (stats[-1]["kernel_launches"] + (2 if planned else 0))
 
     out = None
     if rank == 0:
-        peak = probe_peak(P, torch)
-        achieved = products / (kern_ms * 1e-3)
-        kname = "k_direct" if stats[-1]["strategy"] == "direct" else "k_range_sort"
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": UNIT, "frac": achieved / peak,
-                "traffic": traffic_for(kname, "dense4v_m61" if args.workload == "dense4v" else args.workload),
-                "kernel": kname,
-                "range_step_ms": statistics.mean(s["ms_range_step"] for s in stats),
-                "kernel_ms": kern_ms, "kernel_share_of_step": kern_ms / ms_step,
-                "peak_source": "measured on this GPU in this run: register-only M61 multiply-accumulate probe "
-                               "(key add + 61x61 product + Mersenne fold + modular add per term product; the "
-                               "64x64->128 form, which measures faster in this probe than the 31-bit split form)"}
+        op = oprate_peak(P, torch)
+        probe = probe_peak(P, torch)
+        kname = {"direct": "k_direct", "sort": "k_range_sort", "hash": "k_hash"}[stats[-1]["strategy"]]
+        roof = kernel_roofline(products, kern_ms, ms_step, kname, name, op, probe,
+                               statistics.mean(s["ms_range_step"] for s in stats))
         if planned:
-            e2e_ms, h2d, d2h = e2e_plan(P, torch, w, max(5, min(args.steps, 50)), 3)
+            e2e_ms, h2d, d2h = e2e_plan(P, torch, w, max(5, min(args.steps, 30)), 3)
         else:
-            e2e_ms, h2d, d2h = e2e_product(P, torch, w, max(5, min(args.steps, 50)), 3)
+            e2e_ms, h2d, d2h = e2e_product(P, torch, w, max(5, min(args.steps, 30)), 3)
         e2e_val = products / (statistics.mean(e2e_ms) * 1e-3)
-        extras = {"dense4v_plain_call": {"value": products / (statistics.mean(ms_plain) * 1e-3), "unit": UNIT,
-                                    "ms_per_step": statistics.mean(ms_plain),
-                                    "host_syncs_per_step": stats[-1]["host_syncs"],
-                                    "api": "pm_polymul (host reads sizes between steps)"}}
+        extras = {f"{name}_plain_call": {"value": products / (statistics.mean(ms_plain) * 1e-3), "unit": UNIT,
+                                         "ms_per_step": statistics.mean(ms_plain),
+                                         "host_syncs_per_step": stats[-1]["host_syncs"],
+                                         "api": "pm_polymul (host reads sizes between steps)"}}
         # the secondary workloads run on one GPU only (with N ranks the
         # others would wait for rank 0 at the closing barrier)
         if not args.no_extras and world == 1:
-            wi = polygen.workload_dense4v("i64")
-            ms_i, st_i, _ = time_product(P, torch, wi, 20, 3, flush, kind="i64")
-            extras["dense4v_int64_acc128"] = {"value": wi.term_products / (statistics.mean(ms_i) * 1e-3), "unit": UNIT,
-                                         "ms_per_step": statistics.mean(ms_i),
-                                         "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_i)}
-            w3 = polygen.workload_sparse5v()
-            if not args.no_tune:
-                f3 = _dev(torch, np, w3.f)
-                g3 = _dev(torch, np, w3.g)
-                P.autotune(w3.field_bits, f3[0], f3[1], g3[0], g3[1])
-            ms_3, st_3, r3 = time_product(P, torch, w3, 5, 2, flush)
-            extras["sparse5v_50000x50000"] = {
-                "value": w3.term_products / (statistics.mean(ms_3) * 1e-3), "unit": UNIT,
-                "ms_per_step": statistics.mean(ms_3), "n_out": r3.n,
-                "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_3),
-                "kernel_frac_of_probe": w3.term_products / (statistics.mean(s["ms_range_kernel"] for s in st_3) * 1e-3) / peak}
-            # the paper's Example 1 at full size (Sec. 6): 1.84e10 term products
-            we = polygen.paper_example1()
-            pe = time_plan(P, torch, we, 5, 2, flush)
-            if pe:
-                extras["paper_example1"] = {
-                    "value": we.term_products / (statistics.mean(pe[0]) * 1e-3), "unit": UNIT,
-                    "ms_per_step": statistics.mean(pe[0]), "n_out": pe[1], "term_products": we.term_products,
-                    "workload": "f1 = (1+x+y+z+t)^40 times f1 + 1, mod 2^61-1 (plan replay)",
-                    "frac_of_probe": we.term_products / (statistics.mean(pe[0]) * 1e-3) / peak,
-                    "paper_context": "Fermi GPU, FP64 coefficients: 32 s; 64 Xeon cores, integers: 16.1 s (Sec. 6)"}
-            # Examples 2 and 3 (hashed windows; host reads between rounds)
-            ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
-                   "ex3": "Fermi GPU, FP64: 129 s; 64 Xeon cores, integers: 29.7 s (Sec. 6)"}
-            for nm in ("ex2", "ex3"):
-                wx = polygen.paper_example(nm)
-                fx, gx = _dev(torch, np, wx.f), _dev(torch, np, wx.g)
-                capx = {"ex2": 312855140, "ex3": 144049555}[nm] + 16
-                outx = (torch.empty(capx, dtype=torch.int64, device="cuda"),
-                        torch.empty(capx, dtype=torch.int64, device="cuda"))
-                P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
-                tx = []
-                for _ in range(2):
-                    a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    a_.record()
-                    rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
-                    b_.record()
-                    torch.cuda.synchronize()
-                    tx.append(a_.elapsed_time(b_))
-                extras["paper_" + nm] = {
-                    "value": wx.term_products / (statistics.mean(tx) * 1e-3), "unit": UNIT,
-                    "ms_per_step": statistics.mean(tx), "n_out": rx.n, "term_products": wx.term_products,
-                    "strategy": rx.stats["strategy"], "window_rounds": rx.stats["refine_rounds"],
-                    "workload": wx.note, "paper_context": ctx[nm],
-                    "frac_of_probe": wx.term_products / (statistics.mean(tx) * 1e-3) / peak}
-                del fx, gx, outx
-                torch.cuda.empty_cache()
-            sb = bench_batched(P, torch, args.batch_count, tune=not args.no_tune)
-            extras["sparse_batch_4096"] = sb
-            # serving at ~70% of the measured capacity for the request mix:
-            # 95% sparse requests at the batched pass's time per product, 5%
-            # dense ones at the dense step's time
-            t_req = 0.95 * sb["batched_ms"] * 1e-3 / args.batch_count + 0.05 * ms_step * 1e-3
-            rate = 0.7 / t_req
-            extras["serving_mix"] = bench_serving(P, torch, args.serving_count, rate, tune=not args.no_tune)
-        cpu = None if (args.no_cpu or world > 1) else cpu_baseline(w)
-        if cpu is not None:
-            extras["cpu_alg1_threads"] = cpu_alg1(w)
+            try:
+                secondary_workloads(extras, P, torch, np, polygen, args, name, flush, op, probe, ms_step)
+            except Exception as e:  # the headline line still prints; the failure is reported in it
+                extras["secondary_error"] = f"{type(e).__name__}: {e}"
+        cpu = None
+        if not args.no_cpu and world == 1:
+            cpu = cpu_baseline(w, CPU_ROWS[name])
+            extras["cpu_alg1_threads"] = cpu_alg1(w, 5 * CPU_ROWS[name])
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64 mod 2^61-1", "data": "synthetic",
-            "config": {"workload": WORKLOAD if args.workload == "dense4v" else args.workload,
+            "config": {"workload": WORKLOADS[name], "term_products": products,
                        "l2": "flushed between timed steps (256 MiB write, outside the events)",
                        "api": ("pm_plan_run: the whole device path as one CUDA graph, every kernel re-run "
                                "on the resident inputs each step" if planned else "pm_polymul"),
                        "strategy": stats[-1]["strategy"], "ranges": stats[-1]["n_ranges"], "tuned": tuned,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
             "roofline": roof,
-            "cpu_baseline": {k: v for k, v in cpu.items() if k != "n_out"} if cpu else None,
+            "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "clocks": clocks,
             "n_out": r.n,
             "host_syncs_per_step": 1 if planned else stats[-1]["host_syncs"],
+            "oprate": op,
             "extras": extras,
         }
         print(json.dumps(out))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def secondary_workloads(extras, P, torch, np, polygen, args, name, flush, op, probe, ms_head):
+    """The other workloads on this GPU: each config that is not the headline
+    (plan replay and accumulate kernel with their own roofline fractions),
+    the int64 dense product, the paper's Examples 1-3, the batched pass and
+    the serving loop.  Fills `extras` as it goes."""
+    for other in ("dense4v", "sparse4v", "sparse5v"):
+        if other == name:
+            continue
+        wo = _workload(other)
+        if not args.no_tune:
+            fo, go = _dev(torch, np, wo.f), _dev(torch, np, wo.g)
+            P.autotune(wo.field_bits, fo[0], fo[1], go[0], go[1])
+            del fo, go
+        pl = time_plan(P, torch, wo, 20, 3, flush)
+        msp, sto, ro = time_product(P, torch, wo, 10, 3, flush)
+        step = statistics.mean(pl[0]) if pl else statistics.mean(msp)
+        kname = {"direct": "k_direct", "sort": "k_range_sort", "hash": "k_hash"}[sto[-1]["strategy"]]
+        km = statistics.mean(s["ms_range_kernel"] for s in sto)
+        extras[other] = {"workload": WORKLOADS[other], "value": wo.term_products / (step * 1e-3), "unit": UNIT,
+                         "ms_per_step": step, "api": "plan replay" if pl else "pm_polymul",
+                         "plain_call_ms": statistics.mean(msp), "n_out": ro.n, "strategy": sto[-1]["strategy"],
+                         "kernel": kname, "kernel_ms": km,
+                         "kernel_frac": wo.term_products / (km * 1e-3) / op["peak"],
+                         "kernel_frac_of_mac_probe": wo.term_products / (km * 1e-3) / probe,
+                         "traffic": traffic_for(kname, other)}
+    wi = polygen.workload_dense4v("i64")
+    ms_i, st_i, _ = time_product(P, torch, wi, 20, 3, flush, kind="i64")
+    extras["dense4v_int64_acc128"] = {"value": wi.term_products / (statistics.mean(ms_i) * 1e-3), "unit": UNIT,
+                                      "ms_per_step": statistics.mean(ms_i),
+                                      "kernel_ms": statistics.mean(s["ms_range_kernel"] for s in st_i)}
+    # the paper's Example 1 at full size (Sec. 6): 1.84e10 term products
+    we = polygen.paper_example1()
+    pe = time_plan(P, torch, we, 5, 2, flush)
+    if pe:
+        extras["paper_example1"] = {
+            "value": we.term_products / (statistics.mean(pe[0]) * 1e-3), "unit": UNIT,
+            "ms_per_step": statistics.mean(pe[0]), "n_out": pe[1], "term_products": we.term_products,
+            "workload": "f1 = (1+x+y+z+t)^40 times f1 + 1, mod 2^61-1 (plan replay)",
+            "frac": we.term_products / (statistics.mean(pe[0]) * 1e-3) / op["peak"],
+            "paper_context": "Fermi GPU, FP64 coefficients: 32 s; 64 Xeon cores, integers: 16.1 s (Sec. 6)"}
+    # Examples 2 and 3 (hashed windows)
+    ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
+           "ex3": "Fermi GPU, FP64: 129 s; 64 Xeon cores, integers: 29.7 s (Sec. 6)"}
+    for nm in ("ex2", "ex3"):
+        wx = polygen.paper_example(nm)
+        fx, gx = _dev(torch, np, wx.f), _dev(torch, np, wx.g)
+        capx = {"ex2": 312855140, "ex3": 144049555}[nm] + 16
+        outx = (torch.empty(capx, dtype=torch.int64, device="cuda"),
+                torch.empty(capx, dtype=torch.int64, device="cuda"))
+        P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+        tx = []
+        for _ in range(2):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record()
+            rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+            b_.record()
+            torch.cuda.synchronize()
+            tx.append(a_.elapsed_time(b_))
+        extras["paper_" + nm] = {
+            "value": wx.term_products / (statistics.mean(tx) * 1e-3), "unit": UNIT,
+            "ms_per_step": statistics.mean(tx), "n_out": rx.n, "term_products": wx.term_products,
+            "strategy": rx.stats["strategy"], "window_rounds": rx.stats["refine_rounds"],
+            "workload": wx.note, "paper_context": ctx[nm],
+            "frac": wx.term_products / (statistics.mean(tx) * 1e-3) / op["peak"]}
+        del fx, gx, outx
+        torch.cuda.empty_cache()
+    sb = bench_batched(P, torch, args.batch_count, tune=not args.no_tune)
+    extras["sparse_batch_4096"] = sb
+    # serving at ~70% of the measured capacity for the request mix: 95%
+    # sparse requests at the batched pass's time per product, 5% dense ones
+    # at the dense step's time
+    ms_dense = extras["dense4v"]["ms_per_step"] if "dense4v" in extras else ms_head
+    t_req = 0.95 * sb["batched_ms"] * 1e-3 / args.batch_count + 0.05 * ms_dense * 1e-3
+    rate = 0.7 / t_req
+    extras["serving_mix"] = bench_serving(P, torch, args.serving_count, rate, tune=not args.no_tune)
 
 
 def main():

@@ -62,6 +62,7 @@ extern "C" {
 #define PM_ETIMEOUT      -6  /* a bounded device wait gave up                   */
 #define PM_ECUDA         -7  /* a CUDA runtime call failed                      */
 #define PM_EPLAN         -8  /* a plan's inputs no longer match it (pm_plan_*)  */
+#define PM_ECANCELED     -9  /* a serving request was cancelled before admission */
 
 /* ---- types ---------------------------------------------------------------- */
 
@@ -106,9 +107,13 @@ typedef struct pm_terms_out {
 
 /* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
 /* Direct strategy accumulators (mod p kind). */
-#define PM_ACC_AUTO   0  /* limbs when min(n_f, n_g) <= 65537, else wide        */
+#define PM_ACC_AUTO   0  /* direct: three limbs; hash: limbs when
+                            min(n_f, n_g) <= 65537, else wide                   */
 #define PM_ACC_WIDE   1  /* 64-bit sum + 32-bit wrap count per slot             */
 #define PM_ACC_LIMBS  2  /* four 16-bit limbs in 32-bit counters per slot       */
+#define PM_ACC_LIMBS3 3  /* direct: three limbs (22, 21, 21 bits) in 32-bit
+                            counters per slot, normalised between the passes
+                            of at most 1023 rows (any operand sizes)           */
 
 typedef struct pm_options {
     int32_t strategy;          /* PM_STRATEGY_*                                     */
@@ -116,7 +121,8 @@ typedef struct pm_options {
                                   shared memory allows)                            */
     uint32_t chunk;            /* sort: term products per range (<= 4096)            */
     uint32_t ranges_per_sm;    /* direct: groups per SM; sort: unused                 */
-    int32_t accumulator;       /* PM_ACC_*; PM_ACC_LIMBS needs min(n_f, n_g) <= 65537 */
+    int32_t accumulator;       /* PM_ACC_*; PM_ACC_LIMBS needs min(n_f, n_g) <= 65537;
+                                  PM_ACC_LIMBS3 applies to the direct strategy  */
     uint32_t cost_row;         /* direct: group cost model, cost of one row of f
                                   reaching a window, in term products (0 = 3)       */
     uint32_t cost_window;      /* direct: cost of one window in term products
@@ -173,10 +179,107 @@ typedef struct pm_stats {
 int pm_polymul(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
                pm_terms_out *h, const pm_options *opt, pm_stats *stats, void *stream);
 
+/* ---- the product on a caller-owned workspace ----------------------------------
+ *
+ * Alg. 1 (Sec. 2) takes the operands A, B and gives C; its working storage
+ * -- the canonical operands, the splitters S_k, the per-row edges of
+ * FindEdge, the per-interval results D_k before their concatenation -- is
+ * the implementation's.  pm_polymul takes it from the device's stream-
+ * ordered allocator.  For callers that own all device memory (an engine
+ * with its own arena, a framework allocator), the same product runs on a
+ * workspace the caller allocates, and the call itself allocates no device
+ * memory:
+ *
+ *   pm_workspace_size  runs the product once on the given inputs (its own
+ *                      scratch from the stream-ordered allocator, no output
+ *                      written) and reports the workspace bytes a
+ *                      pm_polymul_ws call on the same inputs, options and
+ *                      autotuner state takes, and the result size (so h can
+ *                      be sized too).  The bytes are exact for the direct
+ *                      and sort strategies; for the hashed-window strategy,
+ *                      whose window splits can differ between runs (a window
+ *                      is split when a bounded hash-table probe runs out,
+ *                      which depends on the order of concurrent inserts),
+ *                      they include a margin of one quarter.
+ *   pm_polymul_ws      pm_polymul with every scratch block carved from
+ *                      `workspace` (device memory of workspace_bytes,
+ *                      256-byte aligned).  Running out of workspace returns
+ *                      PM_ENOMEM (h->n = 0) before any kernel touches memory
+ *                      past its end.  The workspace must not be used by
+ *                      anything else until the call's work on `stream` is
+ *                      done (the call synchronises `stream` before a
+ *                      successful return).
+ * Errors are those of pm_polymul, plus PM_EINVAL for a misaligned or null
+ * workspace with nonzero size. */
+int pm_workspace_size(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                      const pm_options *opt, uint64_t *workspace_bytes, uint64_t *n_out, void *stream);
+int pm_polymul_ws(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                  pm_terms_out *h, const pm_options *opt, pm_stats *stats, void *workspace,
+                  uint64_t workspace_bytes, void *stream);
+
+/* ---- slices of the output key space (Alg. 2: one product over several GPUs) --
+ *
+ * Alg. 2 (Sec. 3) spreads one product over N nodes: every node holds A and
+ * B, the intervals [S_k, S_{k+1}) of the first step are split into N
+ * groups of consecutive intervals by their cumulative operation counts
+ * O_k, each node computes the terms of its group, and the slices are
+ * gathered in ascending order.  The groups own disjoint key ranges, so the
+ * gather is a concatenation: no reduction.
+ *
+ *   pm_shard_bounds      the split: bounds[0..nshards] (host) with
+ *                        bounds[0] = 0, bounds[nshards] = 2^64 - 1, and
+ *                        bounds[m] for 0 < m < nshards the first splitter
+ *                        S_k (the Sec. 5 grid over the canonical operands,
+ *                        about 64 intervals per shard) whose count of term
+ *                        products below it reaches m / nshards of all of
+ *                        them.  products[m] (host, optional) receives shard
+ *                        m's term products.  Deterministic: every rank that
+ *                        calls it on the same inputs gets the same bounds.
+ *   pm_polymul_range     pm_polymul restricted to the result terms whose
+ *                        packed key k has key_lo <= k < key_hi; the
+ *                        concatenation of the slices of consecutive bounds
+ *                        is the whole product, bit for bit.  An empty slice
+ *                        gives h->n = 0.  Statistics count the whole
+ *                        product's operands.
+ *   pm_split_cumulative  the host-side rule of the split alone: cum[0..n)
+ *                        ascending cumulative counts at n interval
+ *                        boundaries; cut[0..nshards] receives, for each
+ *                        shard m, the boundary index it starts at: cut[0] =
+ *                        0, cut[nshards] = n - 1, and cut[m] the first index
+ *                        whose count is at least m / nshards of cum[n-1]
+ *                        (never before cut[m-1]).  Host memory only; needs
+ *                        no GPU.
+ * Errors: those of pm_polymul; PM_EINVAL for nshards outside 1..65536, null
+ * arrays, or counts that are not ascending. */
+int pm_shard_bounds(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                    uint32_t nshards, uint64_t *bounds, uint64_t *products, void *stream);
+int pm_polymul_range(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                     uint64_t key_lo, uint64_t key_hi, pm_terms_out *h, const pm_options *opt, pm_stats *stats,
+                     void *stream);
+int pm_split_cumulative(const uint64_t *cum, uint32_t n, uint32_t nshards, uint32_t *cut);
+
 /* Upper bound on the number of result terms: min(n_f * n_g, box) with box =
  * prod_v (max_f e_v + max_g e_v + 1) over the input terms.  Sizes h->cap. */
 int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g,
                  uint64_t *bound, void *stream);
+
+/* The first step of Alg. 1 (Sec. 2) with the almost regular grid of Sec. 5:
+ * for sorted packed keys alpha[0..na) and beta[0..nb) (device, ascending;
+ * the canonical operands), the splitters S -- the grid's points
+ * alpha_i + beta_j and gamma_end = alpha[na-1] + beta[nb-1] + 1 (the
+ * exclusive end of the last interval), sorted and deduplicated -- into
+ * splitters[0..cap) (device).  Grid: rows i = 0, s_i, 2 s_i, ... with
+ * s_i = max(floor(na / l), 1); on them columns j = j0 + m s_j with
+ * s_j = max(floor(nb / l), 1) and j0 = floor(nb / 2l) on every second grid
+ * row, else 0; then the last row and the last column at the same steps
+ * (0-based indexes; columns past the matrix clamped to its last).
+ * *n_out = |S|.  Errors: PM_EINVAL (l outside 1..4096, null pointers, an
+ * operand of 2^31 terms or more), PM_ECAPACITY (*n_out > cap: nothing
+ * written).  na = 0 or nb = 0 gives *n_out = 0.  The interval boundaries of
+ * the sort strategy start from these splitters; the direct strategy samples
+ * its group costs at the same grid points. */
+int pm_grid(const uint64_t *alpha, uint64_t na, const uint64_t *beta, uint64_t nb, uint32_t l, uint64_t *splitters,
+            uint64_t cap, uint64_t *n_out, void *stream);
 
 /* Unpack n packed keys (device) into an n x nvars uint32 exponent matrix
  * (device, row-major).  Inverse of the packing of Sec. 7. */
@@ -391,6 +494,12 @@ int pm_server_create(const pm_server_config *cfg, pm_server **srv);
 /* Queue one product (the descriptor is copied; the device buffers it points
  * to must stay valid until the request completes). */
 int pm_server_submit(pm_server *srv, const pm_batch_item *item, uint64_t tag);
+/* Withdraw a request that has not been admitted yet: it completes at once
+ * (reported by the next pm_server_progress) with status PM_ECANCELED, and
+ * nothing is written to its output.  A request already admitted to the GPU
+ * runs to completion; for it, and for an unknown tag, the call returns
+ * PM_EINVAL.  Only the first queued request with the tag is withdrawn. */
+int pm_server_cancel(pm_server *srv, uint64_t tag);
 /* Reap finished batches, admit and launch queued requests, and return up to
  * `cap` completions.  Never blocks on the device. */
 int pm_server_progress(pm_server *srv, pm_server_done *done, uint32_t cap, uint32_t *n_done);
@@ -419,11 +528,19 @@ void pm_server_destroy(pm_server *srv);
  * the outputs.
  *
  * The first call on a device looks up the device address of the static
- * array (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array, which keeps the
+ * array (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process; make that first call before any stream capture.  A
+ * device reset (cudaDeviceReset) or a switch to another context on the same
+ * device after that first call is not supported: the kept address would no
+ * longer be valid.  Every call shares the array, which keeps the
  * last call's contents (the kernel clears what must start at zero), so calls
  * whose executions overlap on the GPU race: serialise them.  The call
- * synchronises `stream` before it returns. */
+ * synchronises `stream` before it returns.
+ *
+ * When several errors apply they are reported in pm_polymul's order: an
+ * input exponent at its guard bit, then a repeated input monomial whose
+ * int64 sum overflows, then a product exponent at its guard bit, then the
+ * int128 bound rule, then the capacity. */
 #define PM_NOALLOC_MAX_TERMS     4096u
 #define PM_NOALLOC_MAX_PRODUCTS  65536u
 #define PM_NOALLOC_SCRATCH_BYTES (4u << 20)

@@ -18,11 +18,11 @@ LIB_PATH = os.path.join(HERE, "libpolymul.so")
 
 PM_MAX_VARS = 16
 PM_OK, PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND = 0, -1, -2, -3
-PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA, PM_EPLAN = -4, -5, -6, -7, -8
+PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA, PM_EPLAN, PM_ECANCELED = -4, -5, -6, -7, -8, -9
 KIND = {"m61": 0, "i64": 1, "i192": 2}
 STRATEGY = {"auto": 0, "direct": 1, "sort": 2, "hash": 3}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
-ACCUMULATOR = {"auto": 0, "wide": 1, "limbs": 2}
+ACCUMULATOR = {"auto": 0, "wide": 1, "limbs": 2, "limbs3": 3}
 
 
 class pm_packing(C.Structure):
@@ -64,14 +64,19 @@ class PolymulError(RuntimeError):
 
 
 # exported symbols, in include/polymul.h order
-SYMBOLS = ("pm_polymul", "pm_out_bound", "pm_unpack", "pm_pack", "pm_autotune", "pm_batch_autotune",
+SYMBOLS = ("pm_polymul", "pm_workspace_size", "pm_polymul_ws", "pm_shard_bounds", "pm_polymul_range",
+           "pm_split_cumulative", "pm_out_bound", "pm_grid", "pm_unpack", "pm_pack", "pm_autotune", "pm_batch_autotune",
            "pm_batch_plan_create", "pm_batch_plan_run",
            "pm_batch_plan_finish", "pm_batch_plan_destroy", "pm_batch_polymul", "pm_batch_workspace",
-           "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_progress",
+           "pm_batch_enqueue", "pm_batch_collect", "pm_server_create", "pm_server_submit", "pm_server_cancel", "pm_server_progress",
            "pm_server_state", "pm_server_destroy", "pm_polymul_noalloc",
            "pm_plan_create", "pm_plan_run", "pm_plan_finish", "pm_plan_finish_to_host", "pm_plan_captured",
            "pm_plan_destroy",
-           "pm_strerror", "pm_version", "pm_probe_mac")
+           "pm_strerror", "pm_version")
+# exported by libpolymul_probe.so, in include/polymul_probe.h order
+PROBE_SYMBOLS = ("pm_probe_mac", "pm_probe_oprate", "pm_probe_ops_per_step")
+PROBE_LIB_PATH = os.path.join(HERE, "libpolymul_probe.so")
+OP = {"imad_wide": 0, "imad": 1, "iadd3": 2, "lop3": 3, "shf": 4, "mix": 5}
 
 _lib = None
 
@@ -87,8 +92,25 @@ def lib():
         L.pm_polymul.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), P(pm_terms_out),
                                  P(pm_options), P(pm_stats), C.c_void_p]
         L.pm_polymul.restype = C.c_int
+        L.pm_workspace_size.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), P(pm_options),
+                                        P(C.c_uint64), P(C.c_uint64), C.c_void_p]
+        L.pm_workspace_size.restype = C.c_int
+        L.pm_polymul_ws.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), P(pm_terms_out),
+                                    P(pm_options), P(pm_stats), C.c_void_p, C.c_uint64, C.c_void_p]
+        L.pm_polymul_ws.restype = C.c_int
         L.pm_out_bound.argtypes = [P(pm_packing), P(pm_terms_in), P(pm_terms_in), P(C.c_uint64), C.c_void_p]
         L.pm_out_bound.restype = C.c_int
+        L.pm_shard_bounds.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), C.c_uint32,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]
+        L.pm_shard_bounds.restype = C.c_int
+        L.pm_polymul_range.argtypes = [P(pm_packing), C.c_int, P(pm_terms_in), P(pm_terms_in), C.c_uint64,
+                                       C.c_uint64, P(pm_terms_out), P(pm_options), P(pm_stats), C.c_void_p]
+        L.pm_polymul_range.restype = C.c_int
+        L.pm_split_cumulative.argtypes = [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p]
+        L.pm_split_cumulative.restype = C.c_int
+        L.pm_grid.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_uint64, C.c_uint32, C.c_void_p, C.c_uint64,
+                              P(C.c_uint64), C.c_void_p]
+        L.pm_grid.restype = C.c_int
         L.pm_unpack.argtypes = [P(pm_packing), C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
         L.pm_unpack.restype = C.c_int
         L.pm_pack.argtypes = [P(pm_packing), C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
@@ -100,8 +122,6 @@ def lib():
         L.pm_strerror.restype = C.c_char_p
         L.pm_version.argtypes = []
         L.pm_version.restype = C.c_int
-        L.pm_probe_mac.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]
-        L.pm_probe_mac.restype = C.c_int
         _lib = L
     return _lib
 
@@ -144,11 +164,61 @@ def _terms_in(exps, coefs) -> pm_terms_in:
 
 
 def _check_cuda(*tensors):
+    import torch
+    dev = None
     for x in tensors:
         if not x.is_cuda:
             raise ValueError("inputs must be CUDA tensors")
         if not x.is_contiguous():
             raise ValueError("inputs must be contiguous")
+        if dev is None:
+            dev = torch.cuda.current_device()
+        if x.device.index != dev:
+            raise ValueError(f"tensor on cuda:{x.device.index}, but the current device is cuda:{dev}")
+
+
+WORDS = {"m61": 1, "i64": 2, "i192": 3}
+
+
+def _dtype_names(t) -> str:
+    return str(t.dtype).replace("torch.", "")
+
+
+def check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61") -> None:
+    """Shapes and element types of two operands, checked before any pointer
+    reaches the library: exps (n, nvars) 32-bit integers, coefs (n,) 64-bit
+    integers.  Raises ValueError.  Works on tensors of any device."""
+    if kind not in WORDS:
+        raise ValueError(f"unknown coefficient kind {kind!r}")
+    nv = len(field_bits)
+    for name, e, c in (("f", f_exps, f_coefs), ("g", g_exps, g_coefs)):
+        if e.dim() != 2 or int(e.shape[1]) != nv:
+            raise ValueError(f"{name}_exps must have shape (n, {nv}), got {tuple(e.shape)}")
+        if _dtype_names(e) not in ("int32", "uint32"):
+            raise ValueError(f"{name}_exps must hold 32-bit integers, got {e.dtype}")
+        if c.dim() != 1 or int(c.shape[0]) != int(e.shape[0]):
+            raise ValueError(f"{name}_coefs must have shape ({int(e.shape[0])},), got {tuple(c.shape)}")
+        if _dtype_names(c) not in ("int64", "uint64"):
+            raise ValueError(f"{name}_coefs must hold 64-bit integers, got {c.dtype}")
+
+
+def check_out(out, kind: str = "m61") -> int:
+    """The caller's output pair (keys (cap,), coefs (cap,) for m61 or
+    (cap, words) for the wider kinds), 64-bit integers; returns cap.
+    Raises ValueError.  Works on tensors of any device."""
+    if kind not in WORDS:
+        raise ValueError(f"unknown coefficient kind {kind!r}")
+    keys, coefs = out
+    if keys.dim() != 1 or _dtype_names(keys) not in ("int64", "uint64"):
+        raise ValueError(f"output keys must be a (cap,) tensor of 64-bit integers, got {tuple(keys.shape)} "
+                         f"{keys.dtype}")
+    cap = int(keys.shape[0])
+    words = WORDS[kind]
+    want = (cap,) if words == 1 else (cap, words)
+    if tuple(int(x) for x in coefs.shape) != want or _dtype_names(coefs) not in ("int64", "uint64"):
+        raise ValueError(f"output coefs for kind {kind!r} must be a {want} tensor of 64-bit integers, got "
+                         f"{tuple(coefs.shape)} {coefs.dtype}")
+    return cap
 
 
 @dataclass
@@ -182,8 +252,12 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
     write into (their length is the capacity); otherwise they are allocated
     from pm_out_bound."""
     import torch
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    if out is not None:
+        check_out(out, kind)
+        _check_cuda(out[0], out[1])
     _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
-    words = {"m61": 1, "i64": 2, "i192": 3}[kind]
+    words = WORDS[kind]
     pk = packing(field_bits)
     f = _terms_in(f_exps, f_coefs)
     g = _terms_in(g_exps, g_coefs)
@@ -209,6 +283,123 @@ def polymul(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: s
         raise err
     n = int(h.n)
     return Product(keys[:n], coefs[:n], n, st.as_dict())
+
+
+def shard_bounds(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, nshards: int, kind: str = "m61",
+                 stream=None):
+    """Alg. 2's split of the output key space into ``nshards`` slices of
+    about equal term-product counts (pm_shard_bounds).  Returns (bounds: list
+    of nshards + 1 ints, products: list of nshards ints)."""
+    import numpy as np
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    bounds = np.zeros(nshards + 1, dtype=np.uint64)
+    prods = np.zeros(nshards, dtype=np.uint64)
+    rc = lib().pm_shard_bounds(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), nshards,
+                               bounds.ctypes.data_as(C.c_void_p), prods.ctypes.data_as(C.c_void_p),
+                               _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_shard_bounds")
+    return [int(x) for x in bounds], [int(x) for x in prods]
+
+
+def polymul_range(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, key_lo: int, key_hi: int,
+                  kind: str = "m61", out=None, stream=None, strategy: str = "auto", **opts) -> Product:
+    """The result terms of f * g whose packed key lies in [key_lo, key_hi)
+    (pm_polymul_range).  ``out``: optional (keys, coefs); otherwise sized
+    by pm_out_bound."""
+    import torch
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    if out is not None:
+        check_out(out, kind)
+        _check_cuda(out[0], out[1])
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
+    words = WORDS[kind]
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    if out is None:
+        cap = out_bound(field_bits, f_exps, g_exps, stream)
+        keys = torch.empty(max(cap, 1), dtype=torch.int64, device=f_exps.device)
+        coefs = torch.empty((max(cap, 1), words) if words > 1 else (max(cap, 1),), dtype=torch.int64,
+                            device=f_exps.device)
+    else:
+        keys, coefs = out
+        cap = int(keys.shape[0])
+    h = pm_terms_out(keys.data_ptr(), coefs.data_ptr(), 0, cap)
+    st = pm_stats()
+    o = options(strategy, **opts)
+    rc = lib().pm_polymul_range(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), int(key_lo) & (2**64 - 1),
+                                int(key_hi) & (2**64 - 1), C.byref(h), C.byref(o), C.byref(st),
+                                _stream_handle(stream))
+    if rc != PM_OK:
+        err = PolymulError(rc, "pm_polymul_range")
+        err.needed = int(h.n)
+        raise err
+    n = int(h.n)
+    return Product(keys[:n], coefs[:n], n, st.as_dict())
+
+
+def split_cumulative(cum, nshards: int):
+    """pm_split_cumulative on host arrays (no GPU): the interval boundary
+    index each of ``nshards`` shards starts at, for ascending cumulative
+    operation counts ``cum``.  Returns nshards + 1 ints."""
+    import numpy as np
+    c = np.ascontiguousarray(cum, dtype=np.uint64)
+    cut = np.zeros(nshards + 1, dtype=np.uint32)
+    rc = lib().pm_split_cumulative(c.ctypes.data_as(C.c_void_p), c.size, nshards, cut.ctypes.data_as(C.c_void_p))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_split_cumulative")
+    return [int(x) for x in cut]
+
+
+def workspace_size(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, kind: str = "m61",
+                   strategy: str = "auto", stream=None, **opts):
+    """(workspace bytes, result terms) of the product on these inputs
+    (pm_workspace_size: the product runs once, nothing is written)."""
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs)
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    o = options(strategy, **opts)
+    ws, n = C.c_uint64(0), C.c_uint64(0)
+    rc = lib().pm_workspace_size(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(o), C.byref(ws),
+                                 C.byref(n), _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_workspace_size")
+    return int(ws.value), int(n.value)
+
+
+def polymul_ws(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs, out, workspace,
+               kind: str = "m61", strategy: str = "auto", stream=None, **opts) -> Product:
+    """h = f * g with all scratch carved from ``workspace`` (a CUDA uint8
+    tensor, 256-byte aligned, sized by workspace_size): the call allocates
+    no device memory.  ``out`` = (keys, coefs) supplied by the caller."""
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    cap = check_out(out, kind)
+    _check_cuda(f_exps, f_coefs, g_exps, g_coefs, out[0], out[1], workspace)
+    pk = packing(field_bits)
+    f = _terms_in(f_exps, f_coefs)
+    g = _terms_in(g_exps, g_coefs)
+    h = pm_terms_out()
+    h.keys = out[0].data_ptr()
+    h.coefs = out[1].data_ptr()
+    h.cap = cap
+    st = pm_stats()
+    o = options(strategy, **opts)
+    nbytes = int(workspace.numel()) * int(workspace.element_size())
+    rc = lib().pm_polymul_ws(C.byref(pk), KIND[kind], C.byref(f), C.byref(g), C.byref(h), C.byref(o),
+                             C.byref(st), workspace.data_ptr() if nbytes else None, nbytes, _stream_handle(stream))
+    if rc != PM_OK:
+        err = PolymulError(rc, "pm_polymul_ws")
+        err.needed = int(h.n)
+        raise err
+    n = int(h.n)
+    return Product(out[0][:n], out[1][:n], n, st.as_dict())
 
 
 def _plan_lib():
@@ -246,6 +437,8 @@ class Plan:
     def __init__(self, field_bits, f_exps, f_coefs, g_exps, g_coefs, out, kind: str = "m61",
                  strategy: str = "auto", slots: int = 0, chunk: int = 0, ranges_per_sm: int = 0,
                  accumulator: str = "auto", stream=None):
+        check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+        check_out(out, kind)
         _check_cuda(f_exps, f_coefs, g_exps, g_coefs, out[0], out[1])
         self._keep = (f_exps, f_coefs, g_exps, g_coefs, out)
         self.pk = packing(field_bits)
@@ -308,6 +501,30 @@ class Plan:
             pass
 
 
+def grid(alpha, beta, l: int, stream=None):
+    """Step 1 of Alg. 1 (pm_grid): the Sec. 5 grid's splitters plus
+    gamma_end, sorted and deduplicated, for ascending (n,) int64 tensors of
+    packed keys.  Returns an int64 tensor holding the uint64 splitters."""
+    import torch
+    _check_cuda(alpha, beta)
+    for t in (alpha, beta):
+        if t.dim() != 1 or _dtype_names(t) not in ("int64", "uint64"):
+            raise ValueError("keys must be (n,) tensors of 64-bit integers")
+    na, nb = int(alpha.shape[0]), int(beta.shape[0])
+    n = C.c_uint64(0)
+    L = lib()
+    rc = L.pm_grid(alpha.data_ptr() if na else None, na, beta.data_ptr() if nb else None, nb, l, None, 0,
+                   C.byref(n), _stream_handle(stream))
+    if rc not in (PM_OK, PM_ECAPACITY):
+        raise PolymulError(rc, "pm_grid")
+    out = torch.empty(max(int(n.value), 1), dtype=torch.int64, device=alpha.device)
+    rc = L.pm_grid(alpha.data_ptr() if na else None, na, beta.data_ptr() if nb else None, nb, l, out.data_ptr(),
+                   int(out.shape[0]), C.byref(n), _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_grid")
+    return out[:int(n.value)]
+
+
 def unpack(field_bits: Sequence[int], keys, stream=None):
     """(n,) packed keys -> (n, nvars) int32 exponent tensor."""
     import torch
@@ -335,13 +552,51 @@ def pack(field_bits: Sequence[int], exps, stream=None):
     return keys[:n]
 
 
+_probe_lib = None
+
+
+def probe_lib():
+    """Load libpolymul_probe.so, the roofline's measurement probes (a
+    library of their own, not part of the product's C-ABI)."""
+    global _probe_lib
+    if _probe_lib is None:
+        if not os.path.exists(PROBE_LIB_PATH):
+            raise RuntimeError(f"{PROBE_LIB_PATH} is missing: run paper_1303_7425_gb300.build.build() first")
+        L = C.CDLL(PROBE_LIB_PATH)
+        L.pm_probe_mac.argtypes = [C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]
+        L.pm_probe_mac.restype = C.c_int
+        L.pm_probe_oprate.argtypes = [C.c_int, C.c_uint32, C.c_uint32, C.c_uint64, C.c_uint32, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]
+        L.pm_probe_oprate.restype = C.c_int
+        L.pm_probe_ops_per_step.argtypes = [C.c_int]
+        L.pm_probe_ops_per_step.restype = C.c_uint32
+        _probe_lib = L
+    return _probe_lib
+
+
 def probe_mac(blocks: int, threads: int, iters: int, sink, seed: int = 0x1303742500, stream=None) -> None:
     """Launch the register-only multiply-accumulate probe (see
     include/polymul_probe.h); time it with CUDA events on ``stream``."""
     _check_cuda(sink)
-    rc = lib().pm_probe_mac(blocks, threads, iters, seed, sink.data_ptr(), _stream_handle(stream))
+    rc = probe_lib().pm_probe_mac(blocks, threads, iters, seed, sink.data_ptr(), _stream_handle(stream))
     if rc != PM_OK:
         raise PolymulError(rc, "pm_probe_mac")
+
+
+def probe_oprate(op: str, blocks: int, threads: int, iters: int, sink, clk=None, seed: int = 0x13037425,
+                 stream=None) -> int:
+    """Launch the op-rate probe of instruction class ``op`` (a key of OP);
+    ``clk``: optional (2,) int64 CUDA tensor for the first block's SM cycles
+    and nanoseconds.  Returns the instructions one thread issues per step."""
+    _check_cuda(sink)
+    if clk is not None:
+        _check_cuda(clk)
+    L = probe_lib()
+    rc = L.pm_probe_oprate(OP[op], blocks, threads, iters, seed & 0xFFFFFFFF, sink.data_ptr(),
+                           clk.data_ptr() if clk is not None else None, _stream_handle(stream))
+    if rc != PM_OK:
+        raise PolymulError(rc, "pm_probe_oprate")
+    return int(L.pm_probe_ops_per_step(OP[op]))
 
 
 NOALLOC_MAX_TERMS = 4096
@@ -354,6 +609,8 @@ def polymul_noalloc(field_bits: Sequence[int], f_exps, f_coefs, g_exps, g_coefs,
     allocate device memory: the library allocates nothing (its scratch is a
     static device array); ``out`` = (keys, coefs) tensors supplied by the
     caller.  Returns the number of result terms written."""
+    check_operands(field_bits, f_exps, f_coefs, g_exps, g_coefs, kind)
+    check_out(out, kind)
     _check_cuda(f_exps, f_coefs, g_exps, g_coefs, out[0], out[1])
     pk = packing(field_bits)
     f = _terms_in(f_exps, f_coefs)
@@ -450,15 +707,7 @@ class BatchPlan:
         n = len(products)
         self.items = (pm_batch_item * n)()
         for k, pr in enumerate(products):
-            _check_cuda(pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], pr["out"][0], pr["out"][1])
-            it = self.items[k]
-            it.pk = packing(pr["field_bits"])
-            it.coef_kind = KIND[pr.get("kind", "m61")]
-            it.f = _terms_in(pr["f_exps"], pr["f_coefs"])
-            it.g = _terms_in(pr["g_exps"], pr["g_coefs"])
-            it.h.keys = pr["out"][0].data_ptr()
-            it.h.coefs = pr["out"][1].data_ptr()
-            it.h.cap = int(pr["out"][0].shape[0])
+            self.items[k] = _batch_item(pr)
         self.opt = pm_batch_options(range_target, ranges_per_item)
         self.handle = C.c_void_p()
         rc = _batch_lib().pm_batch_plan_create(self.items, n, C.byref(self.opt), C.byref(self.handle),
@@ -534,6 +783,8 @@ def _server_lib():
         L.pm_server_create.restype = C.c_int
         L.pm_server_submit.argtypes = [C.c_void_p, P(pm_batch_item), C.c_uint64]
         L.pm_server_submit.restype = C.c_int
+        L.pm_server_cancel.argtypes = [C.c_void_p, C.c_uint64]
+        L.pm_server_cancel.restype = C.c_int
         L.pm_server_progress.argtypes = [C.c_void_p, P(pm_server_done), C.c_uint32, P(C.c_uint32)]
         L.pm_server_progress.restype = C.c_int
         L.pm_server_state.argtypes = [C.c_void_p, P(pm_server_state_t)]
@@ -545,6 +796,9 @@ def _server_lib():
 
 
 def _batch_item(pr) -> pm_batch_item:
+    kind = pr.get("kind", "m61")
+    check_operands(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], kind)
+    check_out(pr["out"], kind)
     _check_cuda(pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"], pr["out"][0], pr["out"][1])
     it = pm_batch_item()
     it.pk = packing(pr["field_bits"])
@@ -575,6 +829,10 @@ class Server:
         rc = _server_lib().pm_server_submit(self.handle, C.byref(it), tag)
         if rc != PM_OK:
             raise PolymulError(rc, "pm_server_submit")
+
+    def cancel(self, tag: int) -> bool:
+        """Withdraw a request not yet admitted (True), else False."""
+        return _server_lib().pm_server_cancel(self.handle, tag) == PM_OK
 
     def progress(self):
         n = C.c_uint32()

@@ -1,7 +1,10 @@
-"""Build libpolymul.so (sm_103a) in-tree with nvcc.
+"""Build libpolymul.so and libpolymul_probe.so (sm_103a) in-tree with nvcc.
 
-Each .cu file compiles to an object in parallel, then one shared library is
-linked next to this file.  Usage: ``python -m paper_1303_7425_gb300.build``.
+Each .cu file compiles to an object in parallel, then the shared libraries are
+linked next to this file: libpolymul.so from csrc/*.cu (the product's C-ABI,
+include/polymul.h) and libpolymul_probe.so from csrc/probe/*.cu (the
+roofline's register-only probes, include/polymul_probe.h).  Usage:
+``python -m paper_1303_7425_gb300.build``.
 """
 
 from __future__ import annotations
@@ -19,6 +22,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpolymul.so")
+PROBE_LIB = os.path.join(HERE, "libpolymul_probe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -32,8 +36,8 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found")
 
 
-def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+def _sources(sub=""):
+    return sorted(glob.glob(os.path.join(CSRC, sub, "*.cu")))
 
 
 def _headers():
@@ -48,17 +52,20 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compile both libraries (objects in parallel); returns libpolymul.so's path."""
     os.makedirs(BUILD, exist_ok=True)
-    srcs = _sources()
     hdrs = _headers()
-    objs = []
+    targets = [(LIB, _sources()), (PROBE_LIB, _sources("probe"))]
     jobs = []
-    for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
-        objs.append(o)
-        if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", s, "-o", o]
-            jobs.append(cmd)
+    objs_of = []
+    for _, srcs in targets:
+        objs = []
+        for s in srcs:
+            o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+            objs.append(o)
+            if force or _stale(o, [s] + hdrs):
+                jobs.append([nvcc()] + ARCH + NVCC_FLAGS + list(extra_flags) + ["-c", s, "-o", o])
+        objs_of.append(objs)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for cmd, res in zip(jobs, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs)):
@@ -66,14 +73,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                     sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
                 if res.returncode:
                     raise RuntimeError(f"nvcc failed: {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
-        res = subprocess.run(cmd, capture_output=True, text=True)
-        if res.returncode:
-            sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
-            raise RuntimeError("link failed")
-        os.replace(tmp, LIB)
+    for (lib, _), objs in zip(targets, objs_of):
+        if force or jobs or _stale(lib, objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs
+            res = subprocess.run(cmd, capture_output=True, text=True)
+            if res.returncode:
+                sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
+                raise RuntimeError("link failed")
+            os.replace(tmp, lib)
     return LIB
 
 

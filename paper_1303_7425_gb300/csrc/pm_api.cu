@@ -5,10 +5,12 @@
 // K-e concatenation.  The host only reads sizes and status words between
 // steps; every array the product touches is processed by the kernels.
 #include <cstddef>
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "pm_direct.cuh"
 #include "pm_pack.cuh"
@@ -17,7 +19,9 @@
 
 namespace pm {
 
-bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box, pm_options &o);
+bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 bound, u64 raw_box, pm_options &o);
+int out_bound_and_box(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, u64 *bound, u64 *raw_box,
+                      cudaStream_t s);
 
 constexpr u32 DEFAULT_CHUNK = 4096;    // sort: term products per range
 constexpr u32 MAX_CHUNK = 4096;
@@ -127,12 +131,12 @@ struct Side {
     Ctx c;
     std::unique_ptr<Scratch> S;
     cudaEvent_t ev = nullptr;
-    explicit Side(Ctx &m) : main(m), c(m)
+    Side(Ctx &m, ScratchMode sm) : main(m), c(m)
     {
         c.launches = 0;
         c.syncs = 0;
         c.s = side_stream();
-        S.reset(new Scratch(c.s));
+        S.reset(new Scratch(c.s, sm));
         PM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     void fork()
@@ -235,6 +239,41 @@ static u64 host_rank(const Layout &L, u64 key)
     return r;
 }
 
+// The number of points of the rank box whose packed key is below `key`
+// (any 64-bit value): lexicographic order with x_1 first equals rank order,
+// so the output keys in [klo, khi) are the ranks [rank_below(klo),
+// rank_below(khi)).  A digit at or past its extent means every box point
+// with the same leading digits lies below.
+static u64 rank_below(const Layout &L, u64 key)
+{
+    // bits above the fields (x_1's field ends the packed key) make the key
+    // larger than every monomial of the box
+    const u32 top = L.off[0] + L.width[0];
+    if (top < 64 && (key >> top) != 0) return L.extent[0] * L.stride[0];
+    u64 r = 0;
+    for (u32 v = 0; v < L.nv; v++) {
+        const u64 d = (key >> L.off[v]) & (L.width[v] >= 64 ? ~0ull : ((1ull << L.width[v]) - 1));
+        if (d >= L.extent[v]) return r + L.extent[v] * L.stride[v];
+        r += d * L.stride[v];
+    }
+    return r;
+}
+
+// A slice [lo, hi) of the output key space (pm_polymul_range,
+// pm_shard_bounds); the whole space by default.
+struct KeySlice {
+    u64 lo = 0, hi = ~0ull;
+    bool whole() const { return lo == 0 && hi == ~0ull; }
+};
+
+// What pm_shard_bounds asks of the call: after the canonical operands, the
+// Alg. 2 split into nshards slices, and no product.
+struct ShardQuery {
+    u32 nshards = 0;
+    u64 *bounds = nullptr;    // host, nshards + 1 keys
+    u64 *products = nullptr;  // host, nshards term-product counts (optional)
+};
+
 // K-e for groups/ranges whose scratch slice starts at base[k] - base0
 __global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__restrict__ scoef,
                                  const u64 *__restrict__ base, u64 base0, const u64 *__restrict__ foff,
@@ -258,7 +297,8 @@ __global__ void k_compact_slices(const u64 *__restrict__ skey, const u64 *__rest
 
 static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, const pm_terms_in *g,
                         pm_terms_out *h, const pm_options *opt, pm_stats *st, cudaStream_t stream,
-                        PlanRec *rec = nullptr)
+                        PlanRec *rec = nullptr, ScratchMode smode = ScratchMode(), KeySlice ks = KeySlice(),
+                        ShardQuery *sq = nullptr)
 {
     const bool capture = rec && rec->mode == PlanRec::CAPTURE;
     const u32 *abort = capture ? rec->d_flag : nullptr;
@@ -273,7 +313,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 2 ||
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 3 ||
         o.grid_l > 4096)
         throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
@@ -282,12 +322,12 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     Ctx c;
     c.s = stream;
     device_setup(c);
-    Scratch S(stream);
+    Scratch S(stream, smode);
     Small hs;
     Small *ds = rec ? rec->d_small : S.get<Small>(1);
     PM_CUDA(cudaMemsetAsync(ds, 0, sizeof(Small), c.s));
     if (capture) PM_CUDA(cudaMemsetAsync(rec->d_flag, 0, sizeof(u32), c.s));
-    Side side(c);  // g's steps; destroyed before S
+    Side side(c, smode);  // g's steps; destroyed before S
     auto finish = [&](u64 n_out) {
         h->n = n_out;
         stats.n_out = n_out;
@@ -310,12 +350,13 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     if (f->n == 0 || g->n == 0) return finish(0);
     Layout raw = L;
     const u64 raw_box = set_box(raw, hs.maxe_f, hs.maxe_g);
+    bool tuned = false;
     if (!opt || (!o.strategy && !o.slots && !o.chunk && !o.ranges_per_sm && !o.accumulator && !o.cost_row &&
                  !o.cost_window && !o.grid_l)) {
         // default options: use the autotuner's choice for this shape class
         const unsigned __int128 pr = (unsigned __int128)f->n * g->n;
         const u64 bound = pr < raw_box ? (u64)pr : raw_box;
-        tuned_options(kind, L.nv, f->n, g->n, bound, o);
+        tuned = tuned_options(kind, L.nv, f->n, g->n, bound, raw_box, o);
     }
 
     // K-a (2): canonical operands, their maxima, extremes and sizes    [sync 2]
@@ -362,16 +403,54 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     const u64 products = F.n * G.n;
     stats.term_products = products;
     stats.box = box;
+    if (sq) {
+        // Alg. 2: intervals from the Sec. 5 grid over the canonical
+        // operands (about 64 per shard), their cumulative operation counts
+        // O_k, and the split of the intervals into nshards groups
+        const u64 kend = hs.fl_f[1] + hs.fl_g[1] + 1;
+        u32 l = 1;
+        while ((u64)(l + 1) * (l + 1) < 64ull * sq->nshards && l < 4096) l++;
+        u32 ns = 0;
+        const u64 *Sp = grid_splitters(c, S, F.key, (u32)F.n, G.key, (u32)G.n, l, kend, &ns);
+        u64 *cnt = S.get<u64>(ns);
+        count_below(c, F.key, (u32)F.n, G.key, (u32)G.n, Sp, ns, cnt);
+        std::vector<u64> hS(ns), hc(ns);
+        std::vector<u32> cut(sq->nshards + 1);
+        PM_CUDA(cudaMemcpyAsync(hS.data(), Sp, (size_t)ns * 8, cudaMemcpyDeviceToHost, c.s));
+        PM_CUDA(cudaMemcpyAsync(hc.data(), cnt, (size_t)ns * 8, cudaMemcpyDeviceToHost, c.s));
+        c.sync();
+        split_cumulative(hc.data(), ns, sq->nshards, cut.data());
+        for (u32 m = 0; m <= sq->nshards; m++) sq->bounds[m] = hS[cut[m]];
+        sq->bounds[0] = 0;
+        sq->bounds[sq->nshards] = ~0ull;
+        if (sq->products)
+            for (u32 m = 0; m < sq->nshards; m++) sq->products[m] = hc[cut[m + 1]] - hc[cut[m]];
+        if (sq->products) sq->products[sq->nshards - 1] = products - hc[cut[sq->nshards - 1]];
+        return finish(0);
+    }
+    if (!ks.whole()) {
+        // a slice of the output key space: nothing to do when it misses the
+        // product's keys [first f + first g, last f + last g]
+        const u64 klo = hs.fl_f[0] + hs.fl_g[0], kend = hs.fl_f[1] + hs.fl_g[1] + 1;
+        if (ks.lo >= kend || ks.hi <= klo || ks.lo >= ks.hi) return finish(0);
+    }
     const u32 words = kind == PM_COEF_M61 ? 1 : (kind == PM_COEF_I64_ACC192 ? 3 : 2);
 
     // strategy choice (autotuner defaults)
     int strategy = o.strategy;
+    if (tuned && o.accumulator == PM_ACC_LIMBS && (F.n < G.n ? F.n : G.n) > 65537) o.accumulator = PM_ACC_AUTO;
     const u32 slots_max = direct_max_slots(kind, F.n < G.n ? F.n : G.n, o.accumulator);
     u32 slots = o.slots ? o.slots : slots_max;
+    if (tuned && slots > slots_max) slots = slots_max;  // a class-mate's choice: keep it within this product's limits
     if (slots > slots_max) throw Error(PM_EINVAL, "slots exceed shared memory");
     const u32 chunk = o.chunk ? o.chunk : DEFAULT_CHUNK;
     // direct addressing's FindEdge table has a row of n_f words per window
     const u64 edge_words = ((box + slots - 1) / slots + (u64)c.sm_count * 4 + 1) * F.n;
+    // the tuner's choice was made on another product of this shape class:
+    // if this one cannot take the direct strategy, the automatic choice
+    // below decides instead
+    if (tuned && strategy == PM_STRATEGY_DIRECT && !(box < (1ull << 40) && edge_words <= (1ull << 30)))
+        strategy = PM_STRATEGY_AUTO;
     if (strategy == PM_STRATEGY_AUTO) {
         // direct addressing pays when the rank box is not much larger than
         // the work (every slot of the box is cleared and scanned once) and
@@ -415,8 +494,13 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         u32 *g32 = S.get<u32>(G.n);
         operand_ranks(c, F, L, nullptr);
         operand_ranks(c, G, L, g32);
-        const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
-        const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
+        u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        if (!ks.whole()) {
+            lo = std::max(lo, rank_below(L, ks.lo));
+            end = std::min(end, rank_below(L, ks.hi));
+            if (lo >= end) return finish(0);
+        }
         HashInputs in;
         in.A = F.rank;
         in.Ac = F.coef;
@@ -464,8 +548,13 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         operand_ranks(c, F, L, f32);
         operand_ranks(side.c, G, L, g32);
         side.join();
-        const u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
-        const u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        u64 lo = host_rank(L, hs.fl_f[0]) + host_rank(L, hs.fl_g[0]);
+        u64 end = host_rank(L, hs.fl_f[1]) + host_rank(L, hs.fl_g[1]) + 1;
+        if (!ks.whole()) {
+            lo = std::max(lo, rank_below(L, ks.lo));
+            end = std::min(end, rank_below(L, ks.hi));
+            if (lo >= end) return finish(0);
+        }
         const u32 gps = o.ranges_per_sm ? o.ranges_per_sm : 1;
         u64 G64 = (u64)gps * c.sm_count;
         if (G64 > end - lo) G64 = end - lo;
@@ -522,6 +611,8 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         plan.target = chunk;
         plan.hard_target = true;
         plan.max_rounds = 64;
+        plan.key_lo = ks.lo;
+        plan.key_hi = ks.hi;
         Ranges R = partition(c, S, F.key, (u32)F.n, G.key, (u32)G.n, plan);
         stats.n_ranges = R.n;
         stats.refine_rounds = R.rounds;
@@ -629,8 +720,95 @@ extern "C" int pm_polymul(const pm_packing *pk, int coef_kind, const pm_terms_in
     return rc;
 }
 
-extern "C" int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, uint64_t *bound,
-                            void *stream)
+// The workspace a call on these inputs takes: the product runs once with
+// pool scratch whose blocks are tallied, and writes no output (capacity 0).
+// The hashed-window strategy may split a window more or less often from one
+// run to the next (a window is split when a bounded hash-table probe runs
+// out, and which probe does depends on the order of concurrent inserts), so
+// its tally gets a margin of one quarter.
+extern "C" int pm_workspace_size(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                                 const pm_options *opt, uint64_t *workspace_bytes, uint64_t *n_out, void *stream)
+{
+    if (!workspace_bytes) return PM_EINVAL;
+    *workspace_bytes = 0;
+    if (n_out) *n_out = 0;
+    u64 tally = 0;
+    pm_terms_out h;
+    memset(&h, 0, sizeof(h));
+    pm_stats st;
+    memset(&st, 0, sizeof(st));
+    ScratchMode sm;
+    sm.tally = &tally;
+    int rc = guarded([&] { return polymul_impl(pk, coef_kind, f, g, &h, opt, &st, (cudaStream_t)stream, nullptr, sm); });
+    if (rc != PM_OK && rc != PM_ECAPACITY) return rc;
+    if (st.strategy == PM_STRATEGY_HASH) tally += tally / 4;
+    *workspace_bytes = tally;
+    if (n_out) *n_out = h.n;
+    return PM_OK;
+}
+
+extern "C" int pm_polymul_ws(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                             pm_terms_out *h, const pm_options *opt, pm_stats *stats, void *workspace,
+                             uint64_t workspace_bytes, void *stream)
+{
+    if ((!workspace && workspace_bytes) || ((uintptr_t)workspace & 255u)) {
+        if (h) h->n = 0;
+        return PM_EINVAL;
+    }
+    Arena a;
+    a.base = (char *)workspace;
+    a.size = workspace_bytes;
+    ScratchMode sm;
+    sm.arena = &a;
+    int rc = guarded([&] { return polymul_impl(pk, coef_kind, f, g, h, opt, stats, (cudaStream_t)stream, nullptr, sm); });
+    if (rc != PM_OK && rc != PM_ECAPACITY && h) h->n = 0;
+    return rc;
+}
+
+extern "C" int pm_polymul_range(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                                uint64_t key_lo, uint64_t key_hi, pm_terms_out *h, const pm_options *opt,
+                                pm_stats *stats, void *stream)
+{
+    KeySlice ks;
+    ks.lo = key_lo;
+    ks.hi = key_hi;
+    int rc = guarded([&] {
+        return polymul_impl(pk, coef_kind, f, g, h, opt, stats, (cudaStream_t)stream, nullptr, ScratchMode(), ks);
+    });
+    if (rc != PM_OK && rc != PM_ECAPACITY && h) h->n = 0;
+    return rc;
+}
+
+extern "C" int pm_shard_bounds(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const pm_terms_in *g,
+                               uint32_t nshards, uint64_t *bounds, uint64_t *products, void *stream)
+{
+    if (nshards < 1 || nshards > 65536 || !bounds) return PM_EINVAL;
+    for (u32 m = 0; m <= nshards; m++) bounds[m] = m == nshards ? ~0ull : 0ull;
+    if (products)
+        for (u32 m = 0; m < nshards; m++) products[m] = 0;
+    ShardQuery sq;
+    sq.nshards = nshards;
+    sq.bounds = (u64 *)bounds;
+    sq.products = (u64 *)products;
+    pm_terms_out h;
+    memset(&h, 0, sizeof(h));
+    return guarded([&] {
+        return polymul_impl(pk, coef_kind, f, g, &h, nullptr, nullptr, (cudaStream_t)stream, nullptr, ScratchMode(),
+                            KeySlice(), &sq);
+    });
+}
+
+extern "C" int pm_split_cumulative(const uint64_t *cum, uint32_t n, uint32_t nshards, uint32_t *cut)
+{
+    if (!cum || !cut || nshards < 1 || n < 1) return PM_EINVAL;
+    for (u32 k = 1; k < n; k++)
+        if (cum[k] < cum[k - 1]) return PM_EINVAL;
+    split_cumulative((const u64 *)cum, n, nshards, cut);
+    return PM_OK;
+}
+
+int pm::out_bound_and_box(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, u64 *bound,
+                          u64 *raw_box, cudaStream_t s)
 {
     return guarded([&] {
         validate_packing(pk);
@@ -638,9 +816,10 @@ extern "C" int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm
         validate_terms(g);
         if (!bound) throw Error(PM_EINVAL, "null bound");
         *bound = 0;
+        if (raw_box) *raw_box = 0;
         if (f->n == 0 || g->n == 0) return PM_OK;
         Ctx c;
-        c.s = (cudaStream_t)stream;
+        c.s = s;
         device_setup(c);
         Scratch S(c.s);
         Small hs;
@@ -654,6 +833,46 @@ extern "C" int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm
         u64 box = set_box(L, hs.maxe_f, hs.maxe_g);
         unsigned __int128 prod = (unsigned __int128)f->n * g->n;
         *bound = prod < box ? (u64)prod : box;
+        if (raw_box) *raw_box = box;
+        return PM_OK;
+    });
+}
+
+extern "C" int pm_out_bound(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, uint64_t *bound,
+                            void *stream)
+{
+    u64 b = 0;
+    const int rc = out_bound_and_box(pk, f, g, &b, nullptr, (cudaStream_t)stream);
+    if (bound) *bound = b;
+    return rc;
+}
+
+extern "C" int pm_grid(const uint64_t *alpha, uint64_t na, const uint64_t *beta, uint64_t nb, uint32_t l,
+                       uint64_t *splitters, uint64_t cap, uint64_t *n_out, void *stream)
+{
+    return guarded([&] {
+        if (!n_out) throw Error(PM_EINVAL, "null n_out");
+        *n_out = 0;
+        if (l < 1 || l > 4096) throw Error(PM_EINVAL, "l outside 1..4096");
+        if (na >= (1ull << 31) || nb >= (1ull << 31)) throw Error(PM_EINVAL, "operand too large");
+        if (na == 0 || nb == 0) return PM_OK;
+        if (!alpha || !beta) throw Error(PM_EINVAL, "null keys");
+        if (cap && !splitters) throw Error(PM_EINVAL, "null output");
+        Ctx c;
+        c.s = (cudaStream_t)stream;
+        device_setup(c);
+        Scratch S(c.s);
+        u64 ext[2];
+        PM_CUDA(cudaMemcpyAsync(&ext[0], alpha + na - 1, 8, cudaMemcpyDeviceToHost, c.s));
+        PM_CUDA(cudaMemcpyAsync(&ext[1], beta + nb - 1, 8, cudaMemcpyDeviceToHost, c.s));
+        c.sync();
+        const u64 end = ext[0] + ext[1] + 1;
+        u32 ns = 0;
+        const u64 *Sp = grid_splitters(c, S, (const u64 *)alpha, (u32)na, (const u64 *)beta, (u32)nb, l, end, &ns);
+        *n_out = ns;
+        if (ns > cap) return PM_ECAPACITY;
+        PM_CUDA(cudaMemcpyAsync(splitters, Sp, (size_t)ns * 8, cudaMemcpyDeviceToDevice, c.s));
+        c.sync();
         return PM_OK;
     });
 }
@@ -924,6 +1143,7 @@ extern "C" const char *pm_strerror(int code)
     case PM_ETIMEOUT: return "bounded device wait timed out";
     case PM_ECUDA: return "CUDA runtime error";
     case PM_EPLAN: return "inputs no longer match the plan (re-create it or call pm_polymul)";
+    case PM_ECANCELED: return "request cancelled before admission";
     default: return "unknown error";
     }
 }

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "pm_blocksort.cuh"
+#include "pm_partition.cuh"
 
 namespace pm {
 
@@ -240,37 +241,19 @@ __global__ void __launch_bounds__(PLAN_T) kb_plan(BArgs a)
     const u64 Rs = 4 * R < PLAN_SAMPLES ? 4 * R : PLAN_SAMPLES;
     u32 l = 1;
     while ((u64)(l + 2) * (l + 2) <= Rs) l++;
-    u32 si, sj, Rr, Cc;
-    u64 ns64;
+    GridShape gsh;
     for (;;) {
-        si = cf / l ? cf / l : 1;
-        sj = cg / l ? cg / l : 1;
-        Rr = (cf + si - 1) / si;
-        Cc = (cg + sj - 1) / sj;
-        ns64 = (u64)Rr * Cc + Cc + Rr;
-        if (ns64 <= PLAN_SAMPLES || l == 1) break;
+        gsh = grid_shape(cf, cg, l);
+        if (gsh.total <= PLAN_SAMPLES || l == 1) break;
         l--;
     }
-    const u32 stagger = cg / (2 * l);
-    const u32 ns = (u32)(ns64 < PLAN_SAMPLES ? ns64 : PLAN_SAMPLES);
+    const u32 ns = (u32)(gsh.total < PLAN_SAMPLES ? gsh.total : PLAN_SAMPLES);
     u64 *kA = (u64 *)smem, *kB = kA + PLAN_SAMPLES;
     uint16_t *iA = (uint16_t *)(kB + PLAN_SAMPLES), *iB = iA + PLAN_SAMPLES;
     u32 *hist = (u32 *)(iB + PLAN_SAMPLES);
     for (u32 q = tid; q < ns; q += PLAN_T) {
-        u32 i, j;
-        if (q < Rr * Cc) {
-            const u32 r = q / Cc, c = q % Cc;
-            i = r * si;
-            j = (r & 1) * stagger + c * sj;
-        } else if (q < Rr * Cc + Cc) {
-            i = cf - 1;
-            j = (q - Rr * Cc) * sj;
-        } else {
-            i = (q - Rr * Cc - Cc) * si;
-            j = cg - 1;
-        }
-        if (i > cf - 1) i = cf - 1;
-        if (j > cg - 1) j = cg - 1;
+        u64 i, j;
+        grid_point(gsh, cf, cg, q, i, j);
         kA[q] = A[i] + B[j];
         iA[q] = (uint16_t)q;
     }

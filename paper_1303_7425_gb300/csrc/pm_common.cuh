@@ -55,6 +55,20 @@ __device__ __forceinline__ u64 m61_mul_split(u64 as, u64 bs)
     return t + (m >> 30) + ((m & 0x3FFFFFFFull) << 31);
 }
 
+// a b mod p with three 32 x 32 -> 64 multiplies (Karatsuba's middle term):
+// with a = al + ah 2^31, b = bl + bh 2^31 (al, bl < 2^31; ah, bh < 2^30),
+//     ah bl + al bh = (al + ah)(bl + bh) - al bl - ah bh = m  (< 2^62),
+// where (al + ah)(bl + bh) < 2^64 fits; as in m61_mul_split,
+//     a b = al bl + 2 ah bh + mh + ml 2^31  (mod p),  m = mh 2^30 + ml,
+// and the sum is below 2^63 + 2^62.  sa = al + ah and sb = bl + bh come
+// precomputed with the halves.
+__device__ __forceinline__ u64 m61_mul_k3(u32 al, u32 ah, u32 sa, u32 bl, u32 bh, u32 sb)
+{
+    const u64 p1 = (u64)al * bl, p2 = (u64)ah * bh, p3 = (u64)sa * sb;
+    const u64 m = p3 - p1 - p2;
+    return p1 + 2 * p2 + (m >> 30) + ((m & 0x3FFFFFFFull) << 31);
+}
+
 // any 64-bit x -> [0, p)
 __device__ __forceinline__ u64 m61_reduce(u64 x)
 {
@@ -271,12 +285,33 @@ struct Error : std::runtime_error {
         (ctx).launches++;                                                                  \
     } while (0)
 
+// A caller-provided device workspace carved by a host-side bump pointer
+// (pm_polymul_ws): blocks are 256-byte aligned and never freed; running
+// past the end is PM_ENOMEM before any kernel touches the block.
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    size_t used = 0;
+};
+
+// Where a call's scratch comes from: the stream-ordered pool (default),
+// optionally adding every block's bytes to *tally (the workspace size
+// query), or a caller's arena (no allocation at all).
+struct ScratchMode {
+    Arena *arena = nullptr;
+    u64 *tally = nullptr;
+};
+
+inline size_t scratch_block_bytes(size_t bytes) { return bytes < 256 ? 256 : (bytes + 255) & ~(size_t)255; }
+
 // Stream-ordered scratch: every block comes from cudaMallocAsync on the call's
-// stream and goes back with cudaFreeAsync when the call ends.
+// stream and goes back with cudaFreeAsync when the call ends -- or, in arena
+// mode, from the caller's workspace.
 struct Scratch {
     cudaStream_t s;
+    ScratchMode mode;
     std::vector<void *> blocks;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    explicit Scratch(cudaStream_t st, ScratchMode m = ScratchMode()) : s(st), mode(m) {}
     ~Scratch()
     {
         for (void *p : blocks) cudaFreeAsync(p, s);
@@ -284,15 +319,22 @@ struct Scratch {
     template <class T>
     T *get(size_t n)
     {
+        const size_t bytes = scratch_block_bytes(n * sizeof(T));
+        if (mode.arena) {
+            Arena &a = *mode.arena;
+            if (bytes > a.size - a.used) throw Error(PM_ENOMEM, "workspace too small");
+            void *p = a.base + a.used;
+            a.used += bytes;
+            return (T *)p;
+        }
         void *p = nullptr;
-        size_t bytes = n * sizeof(T);
-        if (bytes < 256) bytes = 256;
         cudaError_t e = cudaMallocAsync(&p, bytes, s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             throw Error(PM_ENOMEM, "cudaMallocAsync failed");
         }
         blocks.push_back(p);
+        if (mode.tally) *mode.tally += bytes;
         return (T *)p;
     }
 };

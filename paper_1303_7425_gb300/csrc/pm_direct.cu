@@ -232,6 +232,14 @@ struct Stream {
     u64 ca;
 };
 
+// The same for the column-record path (ACC_L3): the row's coefficient
+// halves and their sum, and a pointer to the column record of product p
+// that moves with p (the pass's end is kept by the caller).
+struct StreamR {
+    u32 p, r, rend, ra, al, ah, sa;
+    const uint4 *col;
+};
+
 __device__ __forceinline__ void stream_load_row(Stream &c, const DTables &t)
 {
     const uint4 q = t.rec[c.r];
@@ -239,6 +247,37 @@ __device__ __forceinline__ void stream_load_row(Stream &c, const DTables &t)
     c.ra = q.z;
     c.jbase = q.w;
     c.rend = t.off[c.r + 1];
+}
+
+__device__ __forceinline__ void streamr_load_row(StreamR &c, const DTables &t, const uint4 *brec)
+{
+    const uint4 q = t.rec[c.r];
+    c.al = q.x;
+    c.ah = q.y;
+    c.sa = q.x + q.y;
+    c.ra = q.z;
+    c.col = brec + (u32)(q.w + c.p);
+    c.rend = t.off[c.r + 1];
+}
+
+__device__ __forceinline__ void streamr_init(StreamR &c, const DTables &t, u32 nrows, u32 p, u32 end,
+                                             const uint4 *brec)
+{
+    c.p = p;
+    if (p < end) {
+        c.r = d_row_of(t.off, nrows, p);
+        streamr_load_row(c, t, brec);
+    }
+}
+
+__device__ __forceinline__ void streamr_advance_row(StreamR &c, const DTables &t, const uint4 *brec)
+{
+    if (c.p >= c.rend) {
+        do {
+            c.r++;
+        } while (t.off[c.r + 1] <= c.p);
+        streamr_load_row(c, t, brec);
+    }
 }
 
 __device__ __forceinline__ void stream_init(Stream &c, const DTables &t, u32 nrows, u32 p, u32 end)
@@ -275,16 +314,26 @@ __device__ __forceinline__ void stream_advance_row(Stream &c, const DTables &t)
 //   ACC_I192: int64 inputs; 192-bit sum in three words, each word's atomic
 //            add returning the carry into the next, 24 bytes.
 // ---------------------------------------------------------------------------
-enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2, ACC_I192 = 3 };
+//   ACC_L3:  mod p, direct kernel only; the product (< 2^64) split into
+//            limbs of 22, 21 and 21 bits, each added into its own 32-bit
+//            counter with a fire-and-forget reduction, 12 bytes per slot.
+//            A slot receives at most one product per row, and a pass of
+//            the direct kernel stages at most L3_ROWS = 1023 rows; between
+//            passes every slot is normalised (its value mod p split back
+//            into the three limbs, the first below 2^22), so a counter
+//            never exceeds (1 + 1023)(2^22 - 1) < 2^32.  One reduction per
+//            product fewer than ACC_L16, and 4/3 as many slots per window.
+enum { ACC_W64 = 0, ACC_L16 = 1, ACC_I128 = 2, ACC_I192 = 3, ACC_L3 = 4 };
+constexpr u32 L3_ROWS = DROWS - 1;
 
 template <int ACC, u32 STRIDE = 0>
 struct Acc {
-    static constexpr u32 bytes = ACC == ACC_W64 ? 12 : (ACC == ACC_I192 ? 24 : 16);
+    static constexpr u32 bytes = (ACC == ACC_W64 || ACC == ACC_L3) ? 12 : (ACC == ACC_I192 ? 24 : 16);
     static constexpr u32 words = ACC == ACC_I192 ? 3 : (ACC == ACC_I128 ? 2 : 1);  // result words
     // array stride (a window may use fewer slots)
     static constexpr u32 slots = STRIDE ? STRIDE : acc_stride(bytes);
     u64 *w;      // ACC_W64: sums; ACC_I128/I192: word k of slot s at w[k * slots + s]
-    u32 *c;      // ACC_W64: wrap counts; ACC_L16: limb counters, limb k at [k * slots, (k+1) * slots)
+    u32 *c;      // ACC_W64: wrap counts; ACC_L16, ACC_L3: limb counters, limb k at [k * slots, (k+1) * slots)
 
     __device__ __forceinline__ void carve(unsigned char *p)
     {
@@ -301,6 +350,10 @@ struct Acc {
             c[slots + s] = 0;
             c[2 * slots + s] = 0;
             c[3 * slots + s] = 0;
+        } else if (ACC == ACC_L3) {
+            c[s] = 0;
+            c[slots + s] = 0;
+            c[2 * slots + s] = 0;
         } else {
             w[s] = 0;
             w[slots + s] = 0;
@@ -323,9 +376,37 @@ struct Acc {
             atomicAdd(&c[slots + s], (u32)(v >> 16) & 0xFFFFu);
             atomicAdd(&c[2 * slots + s], (u32)(v >> 32) & 0xFFFFu);
             atomicAdd(&c[3 * slots + s], (u32)(v >> 48));
+        } else if (ACC == ACC_L3) {
+            add_l3(s, m61_mul_split(a, b));
         } else {
             add(s, a, b);
         }
+    }
+    __device__ __forceinline__ void add_l3(u32 s, u64 v)
+    {
+        atomicAdd(&c[s], (u32)v & 0x3FFFFFu);
+        atomicAdd(&c[slots + s], (u32)(v >> 22) & 0x1FFFFFu);
+        atomicAdd(&c[2 * slots + s], (u32)(v >> 43));
+    }
+    // the value of three limb counters c0 + c1 2^22 + c2 2^43 (each < 2^32)
+    // mod p: c2 2^43 = (c2 >> 21) 2^64 + (c2 & (2^21 - 1)) 2^43 and
+    // 2^64 = 8 (mod p)
+    static __device__ __forceinline__ u64 l3_value(u32 c0, u32 c1, u32 c2)
+    {
+        const u64 x = (u64)c0 + ((u64)c1 << 22) + 8ull * (c2 >> 21);  // < 2^55
+        const u64 y = (u64)(c2 & 0x1FFFFFu) << 43;                    // < 2^64
+        return m61_add(m61_reduce(x), m61_reduce(y));
+    }
+    // ACC_L3 between passes: the slot's value mod p back in the three limbs
+    __device__ __forceinline__ void normalize(u32 s)
+    {
+        if (ACC != ACC_L3) return;
+        const u32 c0 = c[s], c1 = c[slots + s], c2 = c[2 * slots + s];
+        if ((c0 | c1 | c2) == 0) return;
+        const u64 v = l3_value(c0, c1, c2);
+        c[s] = (u32)v & 0x3FFFFFu;
+        c[slots + s] = (u32)(v >> 22) & 0x1FFFFFu;
+        c[2 * slots + s] = (u32)(v >> 43);
     }
     __device__ __forceinline__ void add(u32 s, u64 a, u64 b)
     {
@@ -339,6 +420,8 @@ struct Acc {
             atomicAdd(&c[slots + s], (u32)(v >> 16) & 0xFFFFu);
             atomicAdd(&c[2 * slots + s], (u32)(v >> 32) & 0xFFFFu);
             atomicAdd(&c[3 * slots + s], (u32)(v >> 48));
+        } else if (ACC == ACC_L3) {
+            add_l3(s, m61_mul_lazy(a, b));
         } else if (ACC == ACC_I128) {
             u64 plo, phi;
             mul_i64_wide((i64)a, (i64)b, plo, phi);
@@ -374,6 +457,10 @@ struct Acc {
             c[slots + s] = (u32)(v0 >> 32);
             c[2 * slots + s] = 0;
             c[3 * slots + s] = 0;
+        } else if (ACC == ACC_L3) {
+            c[s] = (u32)v0;
+            c[slots + s] = (u32)(v0 >> 32);
+            c[2 * slots + s] = 0;
         }
         return nz;
     }
@@ -386,7 +473,7 @@ struct Acc {
         if (ACC == ACC_W64) {
             v0 = w[s];
             w[s] = 0;
-        } else if (ACC == ACC_L16) {
+        } else if (ACC == ACC_L16 || ACC == ACC_L3) {
             v0 = (u64)c[s] | ((u64)c[slots + s] << 32);
             c[s] = 0;
             c[slots + s] = 0;
@@ -418,6 +505,9 @@ struct Acc {
             add128(lo, hi, l3 << 48, l3 >> 16);
             // 2^64 = 8 (mod p); hi < 2^17
             v0 = m61_reduce(m61_reduce(lo) + 8ull * hi);
+            return v0 != 0;
+        } else if (ACC == ACC_L3) {
+            v0 = l3_value(c[s], c[slots + s], c[2 * slots + s]);
             return v0 != 0;
         } else {
             v0 = w[s];
@@ -493,27 +583,30 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                 if (lens[k]) {
                     ras[k] = (u32)__ldg(a.A + i) - (u32)lo;
                     cas[k] = __ldg(a.Ac + i);
-                    if (ACC == ACC_W64 || ACC == ACC_L16) cas[k] = m61_split_row(cas[k]);
+                    if (ACC == ACC_W64 || ACC == ACC_L16 || ACC == ACC_L3) cas[k] = m61_split_row(cas[k]);
                     packed += ((u64)lens[k] << 12) | 1u;
                 }
             }
             u64 ptot;
             const u64 ex = block_exclusive_scan(packed, ptot, ws);
+            // rows per pass: the table's size, one fewer for ACC_L3 (its
+            // counters' bound between normalisations)
+            constexpr u32 RMAX = ACC == ACC_L3 ? L3_ROWS : (u32)DROWS;
             const u32 kept_all = (u32)(ptot & 4095u);
-            const bool cut = kept_all > (u32)DROWS;
+            const bool cut = kept_all > RMAX;
             u32 kept = (u32)(ex & 4095u);
             u32 off = (u32)(ex >> 12);
 #pragma unroll
             for (int k = 0; k < DCAND; k++) {
                 if (lens[k]) {
                     const u32 i = cand + tid * DCAND + k;
-                    if (kept < (u32)DROWS) {
+                    if (kept < RMAX) {
                         t.off[kept] = off;
                         t.rec[kept] = make_uint4((u32)cas[k], (u32)(cas[k] >> 32), ras[k], jls[k] - off);
                         off += lens[k];
-                    } else if (kept == (u32)DROWS) {
+                    } else if (kept == RMAX) {
                         // the first row that does not fit starts the next pass
-                        t.off[DROWS] = off;
+                        t.off[RMAX] = off;
                         s_cand = i;
                     }
                     kept++;
@@ -521,7 +614,7 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             }
             if (!cut && tid == 0) t.off[kept_all] = (u32)(ptot >> 12);
             __syncthreads();
-            const u32 nrows = cut ? (u32)DROWS : kept_all;
+            const u32 nrows = cut ? RMAX : kept_all;
             const u32 next = cut ? s_cand : cand + DCAND * DT;
 
             // warp w takes a contiguous slice of the pass's products; each
@@ -532,6 +625,32 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
             const u32 p0 = w * per_warp;
             const u32 p1 = min(p0 + per_warp, tot);
             const u32 pm = min(p0 + per_warp / 2, p1);
+            if constexpr (ACC == ACC_L3) {
+                // one 16-byte column record per product, through a pointer
+                // that moves with the product index; the product by three
+                // multiplies (m61_mul_k3)
+                StreamR sa, sb;
+                streamr_init(sa, t, nrows, p0 + lane, pm, a.Brec);
+                streamr_init(sb, t, nrows, pm + lane, p1, a.Brec);
+                while (sa.p < pm || sb.p < p1) {
+                    const bool va = sa.p < pm, vb = sb.p < p1;
+                    uint4 qa = make_uint4(0, 0, 0, 0), qb = make_uint4(0, 0, 0, 0);
+                    if (va) {
+                        streamr_advance_row(sa, t, a.Brec);
+                        qa = __ldg(sa.col);
+                    }
+                    if (vb) {
+                        streamr_advance_row(sb, t, a.Brec);
+                        qb = __ldg(sb.col);
+                    }
+                    if (va) acc.add_l3(sa.ra + qa.w, m61_mul_k3(sa.al, sa.ah, sa.sa, qa.x, qa.y, qa.z));
+                    if (vb) acc.add_l3(sb.ra + qb.w, m61_mul_k3(sb.al, sb.ah, sb.sa, qb.x, qb.y, qb.z));
+                    sa.p += 32;
+                    sb.p += 32;
+                    sa.col += 32;
+                    sb.col += 32;
+                }
+            } else {
             Stream sa, sb;
             stream_init(sa, t, nrows, p0 + lane, pm);
             stream_init(sb, t, nrows, pm + lane, p1);
@@ -556,7 +675,14 @@ __global__ void __launch_bounds__(DT, 1) k_direct(DirectArgs a, u32 slots)
                 sa.p += 32;
                 sb.p += 32;
             }
+            }
             __syncthreads();
+            if (ACC == ACC_L3 && next < i1) {
+                // another pass follows: bring every counter back below its
+                // limb's width
+                for (u32 x = tid; x < span; x += DT) acc.normalize(x);
+                __syncthreads();
+            }
             cand = next;
         }
 
@@ -607,6 +733,17 @@ __global__ void k_split_col(const u64 *__restrict__ b, u64 *__restrict__ out, u3
     if (i < n) out[i] = m61_split_col(b[i]);
 }
 
+// g's columns as 16-byte records for m61_mul_k3: the coefficient's 31-bit
+// halves, their sum, and the rank's low 32 bits
+__global__ void k_col_rec(const u64 *__restrict__ b, const u32 *__restrict__ r32, uint4 *__restrict__ out, u32 n)
+{
+    const u32 i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const u64 v = b[i];
+    const u32 bl = (u32)(v & 0x7FFFFFFFull), bh = (u32)(v >> 31);
+    out[i] = make_uint4(bl, bh, bl + bh, r32[i]);
+}
+
 // Order of the windows for the persistent accumulate kernel: descending
 // estimated cost (term products + cost_row rows staged + cost_window), by
 // 64 power-of-two classes -- largest-first scheduling needs no more than an
@@ -643,26 +780,13 @@ __global__ void __launch_bounds__(1024) k_window_order(const u64 *__restrict__ c
 // Weighted histogram of the cost samples over NBK buckets of [lo, end):
 // every grid point of Sec. 5 (steps si, sj, alternate rows shifted by
 // `stagger`, plus the last row and column) adds wg to its bucket.
-__global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, u32 si, u32 sj,
-                            u32 stagger, u32 R, u32 Cc, u64 total, u64 lo, u64 bw, u64 nbk, u64 wg,
-                            u64 *__restrict__ hist)
+__global__ void k_grid_hist(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, GridShape g,
+                            u64 lo, u64 bw, u64 nbk, u64 wg, u64 *__restrict__ hist)
 {
-    u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
+    const u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.total) return;
     u64 i, j;
-    if (p < (u64)R * Cc) {
-        const u64 r = p / Cc, q = p % Cc;
-        i = r * si;
-        j = (r & 1) * stagger + q * sj;
-    } else if (p < (u64)R * Cc + Cc) {
-        i = na - 1;
-        j = (p - (u64)R * Cc) * sj;
-    } else {
-        i = (p - (u64)R * Cc - Cc) * si;
-        j = nb - 1;
-    }
-    if (i > na - 1) i = na - 1;
-    if (j > nb - 1) j = nb - 1;
+    grid_point(g, na, nb, p, i, j);
     u64 k = (A[i] + B[j] - lo) / bw;
     if (k >= nbk) k = nbk - 1;
     atomicAdd(&hist[k], wg);
@@ -865,11 +989,8 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     // cost model: a grid point of the pp-matrix stands for products / ng
     // term products; a bucket also carries its share of the window costs
     // (rows staged and per-window work, k_hist_rows)
-    u32 l = grid_l ? grid_l : 1;
-    u32 si = na / l ? na / l : 1, sj = nb / l ? nb / l : 1;
-    u32 stagger = (u32)(nb / (2ull * l));
-    u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
-    const u64 ng = (u64)R * Cc + Cc + R;
+    const GridShape gs = grid_shape(na, nb, grid_l ? grid_l : 1);
+    const u64 ng = gs.total;
     const u64 span = end - lo;
     const u64 nbk = span < nbk_max ? span : nbk_max;
     const u64 bw = (span + nbk - 1) / nbk;
@@ -877,8 +998,7 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     u64 *hist = S.get<u64>(nbk), *part = S.get<u64>(nparts);
     PM_CUDA(cudaMemsetAsync(hist, 0, nbk * 8, c.s));
     const u64 wg = products / ng + 1;
-    k_grid_hist<<<(unsigned)((ng + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, ng, lo, bw, nbk,
-                                                               wg, hist);
+    k_grid_hist<<<(unsigned)((ng + 255) / 256), 256, 0, c.s>>>(A, na, B, nb, gs, lo, bw, nbk, wg, hist);
     PM_LAUNCHED(c);
     u64 *kw = S.get<u64>(nbk);
     const u64 w = win ? win : 1;
@@ -896,6 +1016,16 @@ u64 *direct_groups(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 n
     return gb;
 }
 
+static int acc_policy(int kind, u64 min_n, int requested);
+
+// the direct kernel's accumulator: three normalised limbs by default (exact
+// for any operand sizes), or the one asked for
+static int direct_acc_policy(int kind, u64 min_n, int requested)
+{
+    if (kind == PM_COEF_M61 && (requested == PM_ACC_AUTO || requested == PM_ACC_LIMBS3)) return ACC_L3;
+    return acc_policy(kind, min_n, requested);
+}
+
 static int acc_policy(int kind, u64 min_n, int requested)
 {
     if (kind == PM_COEF_I64_ACC192) return ACC_I192;
@@ -908,19 +1038,19 @@ static int acc_policy(int kind, u64 min_n, int requested)
     return min_n <= 65537 ? ACC_L16 : ACC_W64;
 }
 
-static u32 acc_bytes(int acc) { return acc == ACC_W64 ? 12 : (acc == ACC_I192 ? 24 : 16); }
+static u32 acc_bytes(int acc) { return (acc == ACC_W64 || acc == ACC_L3) ? 12 : (acc == ACC_I192 ? 24 : 16); }
 
 size_t direct_smem_bytes(u32 slots, int kind, u64 min_n, int requested)
 {
     (void)slots;  // the accumulator arrays always take their full stride
-    const u32 b = acc_bytes(acc_policy(kind, min_n, requested));
+    const u32 b = acc_bytes(direct_acc_policy(kind, min_n, requested));
     return (size_t)acc_stride(b) * b + DTABLE_BYTES;
 }
 
 u32 direct_max_slots(int kind, u64 min_n, int requested)
 {
     // 227 KB of opt-in shared memory per CTA, minus tables and static use
-    return acc_stride(acc_bytes(acc_policy(kind, min_n, requested)));
+    return acc_stride(acc_bytes(direct_acc_policy(kind, min_n, requested)));
 }
 
 template <class K>
@@ -989,8 +1119,13 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 
     // accumulate: persistent CTAs, one per SM; mod-p kinds read g's
     // coefficients split for m61_mul_split
-    const int acc = acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
-    if (acc == ACC_W64 || acc == ACC_L16) {
+    const int acc = direct_acc_policy(kind, a.na < a.nb ? a.na : a.nb, requested);
+    if (acc == ACC_L3) {
+        uint4 *rec = S.get<uint4>(a.nb);
+        k_col_rec<<<(a.nb + 255) / 256, 256, 0, c.s>>>(a.Bc, a.B32, rec, a.nb);
+        PM_LAUNCHED(c);
+        a.Brec = rec;
+    } else if (acc == ACC_W64 || acc == ACC_L16) {
         u64 *bs = S.get<u64>(a.nb);
         k_split_col<<<(a.nb + 255) / 256, 256, 0, c.s>>>(a.Bc, bs, a.nb);
         PM_LAUNCHED(c);
@@ -1005,6 +1140,9 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
     } else if (acc == ACC_L16) {
         set_smem(k_direct<ACC_L16>, bytes);
         k_direct<ACC_L16><<<grid, DT, bytes, c.s>>>(a, slots);
+    } else if (acc == ACC_L3) {
+        set_smem(k_direct<ACC_L3>, bytes);
+        k_direct<ACC_L3><<<grid, DT, bytes, c.s>>>(a, slots);
     } else if (acc == ACC_I128) {
         set_smem(k_direct<ACC_I128>, bytes);
         k_direct<ACC_I128><<<grid, DT, bytes, c.s>>>(a, slots);
@@ -1347,8 +1485,12 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     std::sort(done.begin(), done.end(), [](const Done &x, const Done &y) { return x.lo < y.lo; });
     u64 n_out = 0;
     for (const Done &d : done) n_out += d.n;
-    if (n_out > cap || !hkey) return n_out;
     const u32 ns = (u32)done.size();
+    // the gather's tables are taken before the capacity check, so a call
+    // without room for the result (the workspace size query) takes the
+    // same scratch as one with room
+    u64 *dsrc = S.get<u64>(ns), *dsrcc = S.get<u64>(ns), *ddst = S.get<u64>(ns), *dcn = S.get<u64>(ns);
+    if (n_out > cap || !hkey) return n_out;
     std::vector<u64> src(ns), srcc(ns), dst(ns), cn(ns);
     u64 run = 0;
     for (u32 k = 0; k < ns; k++) {
@@ -1358,7 +1500,6 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         cn[k] = done[k].n;
         run += done[k].n;
     }
-    u64 *dsrc = S.get<u64>(ns), *dsrcc = S.get<u64>(ns), *ddst = S.get<u64>(ns), *dcn = S.get<u64>(ns);
     PM_CUDA(cudaMemcpyAsync(dsrc, src.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
     PM_CUDA(cudaMemcpyAsync(dsrcc, srcc.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));
     PM_CUDA(cudaMemcpyAsync(ddst, dst.data(), ns * 8ull, cudaMemcpyHostToDevice, c.s));

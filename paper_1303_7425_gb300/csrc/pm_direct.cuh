@@ -10,6 +10,7 @@ struct DirectArgs {
     const u64 *A, *Ac;   // f: ranks (sorted), coefficients
     const u64 *B, *Bc;   // g
     const u32 *B32;      // low 32 bits of g's ranks (slot arithmetic is mod 2^32)
+    const uint4 *Brec;   // ACC_L3: per column of g, {b_l, b_h, b_l + b_h, rank} (k_col_rec)
     const u32 *A32;      // f's ranks as u32 when the whole box fits in 32 bits, else null
     u32 na, nb;
     const u64 *gb;       // G + 1 group boundaries (ranks)

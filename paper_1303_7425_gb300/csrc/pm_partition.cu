@@ -49,34 +49,24 @@ __global__ void k_uniform_splitters(u64 lo, u64 end, u64 step, u32 M, u64 *__res
     Sp[m] = (m == M || v > end) ? end : v;
 }
 
-// Sec. 5 grid (1-based i, j in the paper; 0-based here).  Point index p:
-//   p < R*C:               grid row r = p / C, column c = p % C
-//   R*C <= p < R*C + C:    last row, column c
-//   R*C + C <= p < total:  last column, grid row r
-// Columns past n_b are clamped to n_b (duplicates are removed afterwards).
-__global__ void k_grid(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, u32 si, u32 sj,
-                       u32 stagger, u32 R, u32 Cc, u64 total, u64 *__restrict__ out)
+// the Sec. 5 grid's points (grid_point)
+__global__ void k_grid(const u64 *__restrict__ A, u32 na, const u64 *__restrict__ B, u32 nb, GridShape g,
+                       u64 *__restrict__ out)
 {
-    u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= total) return;
+    const u64 p = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.total) return;
     u64 i, j;
-    if (p < (u64)R * Cc) {
-        u64 r = p / Cc, c = p % Cc;
-        i = r * si;
-        j = (r & 1) * stagger + c * sj;
-    } else if (p < (u64)R * Cc + Cc) {
-        i = na - 1;
-        j = (p - (u64)R * Cc) * sj;
-    } else {
-        i = (p - (u64)R * Cc - Cc) * si;
-        j = nb - 1;
-    }
-    if (i > na - 1) i = na - 1;
-    if (j > nb - 1) j = nb - 1;
+    grid_point(g, na, nb, p, i, j);
     out[p] = A[i] + B[j];
 }
 
 __global__ void k_set_u64(u64 *p, u64 v) { *p = v; }
+
+__global__ void k_clamp(u64 *__restrict__ v, size_t n, u64 lo, u64 hi)
+{
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = v[i] < lo ? lo : (v[i] > hi ? hi : v[i]);
+}
 
 __global__ void k_unique_mark(const u64 *__restrict__ v, size_t n, u64 *__restrict__ keep)
 {
@@ -143,14 +133,33 @@ __global__ void k_ranges_emit(const u64 *__restrict__ Sp, const u64 *__restrict_
 
 static unsigned blocks_for(size_t n, int t) { return (unsigned)((n + t - 1) / t ? (n + t - 1) / t : 1); }
 
-void grid_sample(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, u32 si, u32 sj, u32 stagger, u32 R, u32 Cc,
-                 u64 total, u64 *out)
+void grid_sample(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, const GridShape &g, u64 *out)
 {
-    k_grid<<<blocks_for(total, 256), 256, 0, c.s>>>(A, na, B, nb, si, sj, stagger, R, Cc, total, out);
+    k_grid<<<blocks_for(g.total, 256), 256, 0, c.s>>>(A, na, B, nb, g, out);
     PM_LAUNCHED(c);
 }
 
+void split_cumulative(const u64 *cum, u32 ns, u32 nshards, u32 *cut)
+{
+    const u64 total = ns ? cum[ns - 1] : 0;
+    cut[0] = 0;
+    u32 k = 0;
+    for (u32 m = 1; m < nshards; m++) {
+        const unsigned __int128 want = (unsigned __int128)total * m;  // cum[k] * nshards >= total * m
+        while (k + 1 < ns && (unsigned __int128)cum[k] * nshards < want) k++;
+        cut[m] = k;
+    }
+    cut[nshards] = ns ? ns - 1 : 0;
+}
+
+void count_below(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, const u64 *Sp, u32 ns, u64 *cnt);
+
 static void count_at(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, const u64 *Sp, u32 ns, u64 *cnt)
+{
+    count_below(c, A, na, B, nb, Sp, ns, cnt);
+}
+
+void count_below(Ctx &c, const u64 *A, u32 na, const u64 *B, u32 nb, const u64 *Sp, u32 ns, u64 *cnt)
 {
     unsigned g = ns < (u32)(c.sm_count * 16) ? ns : (unsigned)(c.sm_count * 16);
     k_count_below<<<g, KB_THREADS, 0, c.s>>>(A, na, B, nb, Sp, ns, cnt);
@@ -165,6 +174,32 @@ static u64 read_u64(Ctx &c, const u64 *d)
     return h;
 }
 
+u64 *grid_splitters(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, u32 l, u64 end, u32 *ns,
+                    u64 clamp_lo, u64 clamp_hi)
+{
+    const GridShape g = grid_shape(na, nb, l);
+    u64 total = g.total;
+    u64 *cand = S.get<u64>(total + 1);
+    grid_sample(c, A, na, B, nb, g, cand);
+    k_set_u64<<<1, 1, 0, c.s>>>(cand + total, end);  // gamma_end
+    PM_LAUNCHED(c);
+    total += 1;
+    radix_sort_pairs(c, S, cand, nullptr, nullptr, total, bit_length(end));
+    if (clamp_lo != 0 || clamp_hi != ~0ull) {  // monotone: the order holds
+        k_clamp<<<blocks_for(total, 256), 256, 0, c.s>>>(cand, total, clamp_lo, clamp_hi);
+        PM_LAUNCHED(c);
+    }
+    u64 *keep = S.get<u64>(total), *pos = S.get<u64>(total + 1);
+    k_unique_mark<<<blocks_for(total, 256), 256, 0, c.s>>>(cand, total, keep);
+    PM_LAUNCHED(c);
+    scan_exclusive_u64(c, S, keep, pos, total);
+    u64 *Sp = S.get<u64>(total);
+    k_select<<<blocks_for(total, 256), 256, 0, c.s>>>(cand, keep, pos, total, Sp);
+    PM_LAUNCHED(c);
+    *ns = (u32)read_u64(c, pos + total);
+    return Sp;
+}
+
 Ranges partition(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb, const PartitionPlan &plan)
 {
     // host copies of the key extremes (four words)
@@ -174,8 +209,12 @@ Ranges partition(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb,
     PM_CUDA(cudaMemcpyAsync(&ext[2], B, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
     PM_CUDA(cudaMemcpyAsync(&ext[3], B + nb - 1, sizeof(u64), cudaMemcpyDeviceToHost, c.s));
     c.sync();
-    const u64 lo = ext[0] + ext[2];
-    const u64 end = ext[1] + ext[3] + 1;  // gamma_end: one past the largest product key
+    u64 lo = ext[0] + ext[2];
+    u64 end = ext[1] + ext[3] + 1;  // gamma_end: one past the largest product key
+    // a slice of the output key space: the caller checked it is not empty
+    if (plan.key_lo > lo) lo = plan.key_lo;
+    if (plan.key_hi < end) end = plan.key_hi;
+    if (lo >= end) throw Error(PM_ECUDA, "empty key slice reached the partition");
 
     u64 *Sp = nullptr;
     u32 ns = 0;  // number of boundaries (ranges + 1)
@@ -188,25 +227,7 @@ Ranges partition(Ctx &c, Scratch &S, const u64 *A, u32 na, const u64 *B, u32 nb,
         PM_LAUNCHED(c);
     } else {
         // Sec. 5 grid with parameter l, steps clamped to >= 1
-        u32 l = plan.grid_l ? plan.grid_l : 1;
-        u32 si = na / l ? na / l : 1, sj = nb / l ? nb / l : 1;
-        u32 stagger = (u32)(nb / (2ull * l));
-        u32 R = (na + si - 1) / si, Cc = (nb + sj - 1) / sj;
-        u64 total = (u64)R * Cc + Cc + R;
-        u64 *cand = S.get<u64>(total + 1);
-        grid_sample(c, A, na, B, nb, si, sj, stagger, R, Cc, total, cand);
-        k_set_u64<<<1, 1, 0, c.s>>>(cand + total, end);  // gamma_end
-        PM_LAUNCHED(c);
-        total += 1;
-        radix_sort_pairs(c, S, cand, nullptr, nullptr, total, bit_length(end));
-        u64 *keep = S.get<u64>(total), *pos = S.get<u64>(total + 1);
-        k_unique_mark<<<blocks_for(total, 256), 256, 0, c.s>>>(cand, total, keep);
-        PM_LAUNCHED(c);
-        scan_exclusive_u64(c, S, keep, pos, total);
-        Sp = S.get<u64>(total);
-        k_select<<<blocks_for(total, 256), 256, 0, c.s>>>(cand, keep, pos, total, Sp);
-        PM_LAUNCHED(c);
-        ns = (u32)read_u64(c, pos + total);
+        Sp = grid_splitters(c, S, A, na, B, nb, plan.grid_l ? plan.grid_l : 1, ext[1] + ext[3] + 1, &ns, lo, end);
     }
 
     // count, then refine ranges above the target

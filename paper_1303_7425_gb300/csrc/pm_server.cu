@@ -359,6 +359,33 @@ extern "C" int pm_server_submit(pm_server *s, const pm_batch_item *item, uint64_
     return PM_OK;
 }
 
+extern "C" int pm_server_cancel(pm_server *s, uint64_t tag)
+{
+    if (!s) return PM_EINVAL;
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+        if (it->tag == tag) {
+            const Req r = *it;
+            s->pending.erase(it);
+            fail_now(s, r, PM_ECANCELED);
+            return PM_OK;
+        }
+    Req r;
+    bool found = false;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto it = s->big.begin(); it != s->big.end(); ++it)
+            if (it->tag == tag) {
+                r = *it;
+                s->big.erase(it);
+                found = true;
+                break;
+            }
+    }
+    if (!found) return PM_EINVAL;  // unknown, already admitted, or done
+    fail_now(s, r, PM_ECANCELED);
+    return PM_OK;
+}
+
 extern "C" int pm_server_progress(pm_server *s, pm_server_done *out, uint32_t cap, uint32_t *n_done)
 {
     if (!s || !n_done || (cap && !out)) return PM_EINVAL;

@@ -21,13 +21,16 @@
 
 namespace pm {
 
+// A shape class: kind, nvars, floor(log2) of n_f, n_g, the result bound
+// min(n_f n_g, box) and the inputs' exponent box itself (so products with
+// the same sizes but boxes of very different sparsity tune apart).
 struct ShapeKey {
     int kind;
     u32 nvars;
-    int lf, lg, lbox;
+    int lf, lg, lbound, lbox;
     bool operator<(const ShapeKey &o) const
     {
-        return std::tie(kind, nvars, lf, lg, lbox) < std::tie(o.kind, o.nvars, o.lf, o.lg, o.lbox);
+        return std::tie(kind, nvars, lf, lg, lbound, lbox) < std::tie(o.kind, o.nvars, o.lf, o.lg, o.lbound, o.lbox);
     }
 };
 
@@ -44,18 +47,22 @@ static int log2i(u64 x)
     return b;
 }
 
-ShapeKey shape_key(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box)
+ShapeKey shape_key(int kind, u32 nvars, u64 nf, u64 ng, u64 bound, u64 raw_box)
 {
-    return ShapeKey{kind, nvars, log2i(nf), log2i(ng), log2i(raw_box)};
+    return ShapeKey{kind, nvars, log2i(nf), log2i(ng), log2i(bound), log2i(raw_box)};
 }
+
+// pm_out_bound's value and the inputs' exponent box (pm_api.cu)
+int out_bound_and_box(const pm_packing *pk, const pm_terms_in *f, const pm_terms_in *g, u64 *bound, u64 *box,
+                      cudaStream_t s);
 
 // used by pm_polymul when its options are all defaults
 u32 batch_range_chunk(u32 cw);  // pm_batch.cu
 
-bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 raw_box, pm_options &o)
+bool tuned_options(int kind, u32 nvars, u64 nf, u64 ng, u64 bound, u64 raw_box, pm_options &o)
 {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find(shape_key(kind, nvars, nf, ng, raw_box));
+    auto it = g_tuned.find(shape_key(kind, nvars, nf, ng, bound, raw_box));
     if (it == g_tuned.end()) return false;
     o = it->second;
     return true;
@@ -103,12 +110,9 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
 {
     if (!pk || !f || !g || !h || !best) return PM_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    uint64_t bound = 0;
-    int rc = pm_out_bound(pk, f, g, &bound, stream);
+    u64 bound = 0, raw_box = 0;
+    int rc = out_bound_and_box(pk, f, g, &bound, &raw_box, s);
     if (rc != PM_OK) return rc;
-    // the shape class's last coordinate: min(n_f n_g, exponent box of the
-    // inputs), pm_out_bound's value
-    const u64 raw_box = bound;
 
     std::vector<pm_options> cand;
     auto add = [&](int strategy, u32 slots, u32 gps, int acc, u32 chunk, u32 crow = 0, u32 cwin = 0, u32 grid_l = 0) {
@@ -164,7 +168,7 @@ extern "C" int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_i
     *best = cand[best_k];
     rep.best = (uint32_t)best_k;
     if (report) *report = rep;
-    remember(shape_key(coef_kind, pk->nvars, f->n, g->n, raw_box), *best);
+    remember(shape_key(coef_kind, pk->nvars, f->n, g->n, bound, raw_box), *best);
     return PM_OK;
 }
 

@@ -24,6 +24,7 @@ STRATS = [
     dict(strategy="direct"),
     dict(strategy="direct", accumulator="wide"),
     dict(strategy="direct", accumulator="limbs", slots=2048),
+    dict(strategy="direct", accumulator="limbs3", slots=3000),
     dict(strategy="direct", slots=512),            # many ranges, ragged tails
     dict(strategy="direct", slots=1000, ranges_per_sm=64),
     dict(strategy="direct", ranges_per_sm=3, cost_row=1, cost_window=1),   # other group boundaries
@@ -123,6 +124,26 @@ def test_direct_every_row_has_products(nf, ng, slots, kind):
     if slots:
         opts["slots"] = slots
     gpu = run_gpu(w.field_bits, kind, fe, fc, ge, gc, **opts)
+    assert gpu[2]["strategy"] == "direct"
+    assert_same(gpu, _oracle(w), w.field_bits)
+
+
+@pytest.mark.parametrize("acc", ["limbs3", "limbs", "wide"])
+def test_direct_counters_at_their_bound(acc):
+    """Every coefficient p - 1 or a value whose split form makes the largest
+    limbs, univariate operands of 5000 terms: the middle slots receive
+    5000 products each, over five passes of at most 1023 rows, so the
+    three-limb counters reach their bound between normalisations."""
+    nf = ng = 5000
+    P61 = (1 << 61) - 1
+    fe = np.arange(nf, dtype=np.uint32).reshape(-1, 1)
+    ge = np.arange(ng, dtype=np.uint32)[::-1].copy().reshape(-1, 1)
+    # the largest residues and the extreme 31-bit halves of the split form
+    big = [P61 - 1, P61 - 2, (((1 << 30) - 1) << 31) + 5, (1 << 31) - 1]
+    fc = np.array([big[i % 4] for i in range(nf)], dtype=np.uint64)
+    gc = np.array([big[(i + 1) % 4] for i in range(ng)], dtype=np.uint64)
+    w = polygen.Workload("uni_max", 1, [16], "m61", polygen.Poly(fe, fc), polygen.Poly(ge, gc))
+    gpu = run_gpu(w.field_bits, "m61", fe, fc, ge, gc, strategy="direct", accumulator=acc)
     assert gpu[2]["strategy"] == "direct"
     assert_same(gpu, _oracle(w), w.field_bits)
 

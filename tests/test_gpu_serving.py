@@ -92,3 +92,41 @@ def test_serving_budget_admission():
         e, c = oracle.mul(w.nvars, w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
         n = rep["done"][k]["n"]
         np.testing.assert_array_equal(prods[k]["out"][1][:n].cpu().numpy().view(np.uint64), c)
+
+
+def test_serving_cancellation():
+    """Requests withdrawn before admission complete with PM_ECANCELED and
+    leave their outputs untouched; the others complete exactly as computed
+    alone; a tag that is unknown or already admitted cannot be cancelled."""
+    import time
+
+    import paper_1303_7425_gb300 as P
+    ws, _ = _stream(count=30, dense=0, seed=31, rate=1e6, hi=300)
+    prods = [_prod(w) for w in ws]
+    srv = P.Server(device_budget=1 << 30, streams=2, max_batch=8)
+    try:
+        for k, pr in enumerate(prods):
+            srv.submit(pr, k)
+        cancel = set(range(1, 30, 3))
+        for k in sorted(cancel):
+            assert srv.cancel(k)
+        assert not srv.cancel(1000)                  # unknown tag
+        done = {}
+        t0 = time.time()
+        while len(done) < len(ws) and time.time() - t0 < 60:
+            for d in srv.progress():
+                done[d["tag"]] = d
+        assert len(done) == len(ws)
+        assert not srv.cancel(0)                     # finished: nothing to withdraw
+    finally:
+        srv.close()
+    for k, pr in enumerate(prods):
+        if k in cancel:
+            assert done[k]["status"] == -9 and done[k]["n"] == 0
+            assert bool((pr["out"][0] == -1).all()) and bool((pr["out"][1] == -1).all())
+        else:
+            assert done[k]["status"] == 0
+            alone = P.polymul(pr["field_bits"], pr["f_exps"], pr["f_coefs"], pr["g_exps"], pr["g_coefs"])
+            n = done[k]["n"]
+            assert alone.n == n
+            np.testing.assert_array_equal(alone.coefs.cpu().numpy(), pr["out"][1][:n].cpu().numpy())
