@@ -254,23 +254,24 @@ def probe_peak(P, torch):
 
 
 def oprate_peak(P, torch):
-    """The integer-op bound of one term product, derived from measured
-    instruction rates (register-only probes, pm_probe_oprate): per SM and
-    clock, r_wide 32x32->64 multiply-adds, r_simple simple ops (the fastest
-    of three-input add, three-input logic op and funnel shift) and the issue
-    limit of 128 lane-instructions.  A term product needs OPS_WIDE wide
-    multiplies and OPS_SIMPLE simple ops, so an SM needs at least
-    max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple, (OPS_WIDE + OPS_SIMPLE) / 128)
-    clocks per product.  The bound is SMs x clock / that; the measured rate
-    of the same 4:14 mix on independent chains is reported beside it, and
-    the larger of the two is the peak."""
+    """The integer-op bound of one term product, from instruction rates
+    measured on this GPU (register-only probes, pm_probe_oprate) and the
+    pipes they run on.  On GB300 the simple ops (three-input add and logic
+    op, funnel shift) issue to the ALU pipe and the multiplies to the
+    FMA-heavy pipe, each about 64 lanes per SM per clock; a 32 x 32 -> 64
+    multiply keeps the FMA-heavy pipe twice as long as a 32-bit one; an SM
+    issues at most 128 lane-instructions per clock.  A term product needs
+    OPS_WIDE wide multiplies and OPS_SIMPLE simple ops, so an SM needs at
+    least max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple,
+    (OPS_WIDE + OPS_SIMPLE) / 128) clocks per product, with r_wide the
+    larger of the measured wide rate and half the 32-bit multiply rate."""
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     blocks, threads = sms * 4, 256
     sink = torch.empty(blocks * threads, dtype=torch.int64, device="cuda")
     clk = torch.zeros(2, dtype=torch.int64, device="cuda")
     rates, mhz = {}, []
-    for op in ("imad_wide", "imad", "iadd3", "lop3", "shf", "mix"):
-        iters = (1 << 15) if op == "mix" else (1 << 16)
+    for op in ("imad_wide", "imad", "imad_hi", "iadd3", "lop3", "shf"):
+        iters = 1 << 16
         P.probe_oprate(op, blocks, threads, iters >> 4, sink, clk)      # warm-up
         torch.cuda.synchronize()
         best = None
@@ -289,19 +290,12 @@ def oprate_peak(P, torch):
                 best = (per_sm_clk, ops / (ms * 1e-3), f_ghz * 1e3)
         rates[op] = {"per_sm_per_clk": best[0], "lane_ops_per_s": best[1], "sm_mhz": best[2]}
         mhz.append(best[2])
-    r_wide = rates["imad_wide"]["per_sm_per_clk"]
     r_simple = max(rates[k]["per_sm_per_clk"] for k in ("iadd3", "lop3", "shf"))
-    # the measured mix decides whether the classes overlap: on this GPU it
-    # runs at the sum of the per-class times (one shared integer pipe), so
-    # the bound adds them; the overlapped bound (each class on a pipe of its
-    # own, issue-limited) is reported beside it
-    clk_add = OPS_WIDE / r_wide + OPS_SIMPLE / r_simple
-    clk_overlap = max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple, (OPS_WIDE + OPS_SIMPLE) / ISSUE_LANES_PER_CLK)
+    r_wide = max(rates["imad_wide"]["per_sm_per_clk"], rates["imad"]["per_sm_per_clk"] / 2)
+    clk_per_product = max(OPS_WIDE / r_wide, OPS_SIMPLE / r_simple, (OPS_WIDE + OPS_SIMPLE) / ISSUE_LANES_PER_CLK)
     f_mhz = statistics.median(mhz)
-    model = sms * f_mhz * 1e6 / clk_add
-    mix = rates["mix"]["lane_ops_per_s"] / (OPS_WIDE + OPS_SIMPLE)
-    return {"peak": max(model, mix), "model": model, "mix_measured": mix, "clk_per_product_per_sm": clk_add,
-            "overlap_bound": sms * f_mhz * 1e6 / clk_overlap,
+    peak = sms * f_mhz * 1e6 / clk_per_product
+    return {"peak": peak, "clk_per_product_per_sm": clk_per_product, "r_wide": r_wide, "r_simple": r_simple,
             "sm_mhz": f_mhz, "sms": sms, "ops_per_product": {"wide_multiply": OPS_WIDE, "simple": OPS_SIMPLE},
             "rates": {k: round(v["per_sm_per_clk"], 2) for k, v in rates.items()}}
 
@@ -607,13 +601,11 @@ def kernel_roofline(products, kern_ms, step_ms, kname, traffic_key, op, probe, r
             "traffic": traffic_for(kname, traffic_key), "kernel": kname,
             "kernel_ms": kern_ms, "range_step_ms": range_step_ms, "kernel_share_of_step": kern_ms / step_ms,
             "peak_source": ("derived from instruction rates measured on this GPU in this run (register-only "
-                            "probes): %d wide multiplies + %d simple ops per term product at %.1f / %.1f lane-ops "
-                            "per SM per clock (wide / simple), times added (the measured 4:14 mix runs at the sum: "
-                            "%.3g products/s), %d SMs at %.0f MHz; if the classes overlapped the bound would be "
-                            "%.3g" % (OPS_WIDE, OPS_SIMPLE, op["rates"]["imad_wide"],
-                                      max(op["rates"][k] for k in ("iadd3", "lop3", "shf")), op["mix_measured"],
-                                      op["sms"], op["sm_mhz"], op["overlap_bound"])),
-            "frac_of_overlap_bound": achieved / op["overlap_bound"],
+                            "probes): %d wide multiplies + %d simple ops per term product; wide multiplies at "
+                            "%.1f, simple ops at %.1f lane-ops per SM per clock (FMA-heavy and ALU pipes), issue "
+                            "limit 128; %.3f clocks per product per SM, %d SMs at %.0f MHz"
+                            % (OPS_WIDE, OPS_SIMPLE, op["r_wide"], op["r_simple"], op["clk_per_product_per_sm"],
+                               op["sms"], op["sm_mhz"])),
             "frac_of_mac_probe": achieved / probe, "mac_probe": probe}
 
 

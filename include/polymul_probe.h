@@ -9,10 +9,10 @@
  *                    product that advance the operand;
  *   pm_probe_oprate  the throughput of one integer instruction class at a
  *                    time (32 x 32 -> 64 multiply-add, 32-bit multiply-add,
- *                    three-input add, three-input logic op, funnel shift)
- *                    and of the algorithmic mix of one term product (4 wide
- *                    multiplies + 14 simple ops), from which the benchmark
- *                    derives the integer-op bound per term product.
+ *                    three-input add, three-input logic op, funnel shift,
+ *                    high half of a 32 x 32 multiply), from which the
+ *                    benchmark derives the integer-op bound per term product
+ *                    (4 wide multiplies + 14 simple ops).
  */
 #ifndef POLYMUL_PROBE_H
 #define POLYMUL_PROBE_H
@@ -29,7 +29,7 @@ extern "C" {
 #define PM_OP_IADD3     2  /* three-input 32-bit add                             */
 #define PM_OP_LOP3      3  /* three-input 32-bit logic op                        */
 #define PM_OP_SHF       4  /* 32-bit funnel shift                                */
-#define PM_OP_MIX       5  /* 4 mad.wide + 7 three-input adds + 7 logic ops      */
+#define PM_OP_IMAD_HI   6  /* mad.hi.u32: high half of a 32 x 32 multiply, added */
 
 /* Launch blocks x threads threads; each performs `iters` iterations of 4
  * independent multiply-accumulate chains (4 * iters term products) and

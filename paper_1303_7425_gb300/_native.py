@@ -76,7 +76,7 @@ SYMBOLS = ("pm_polymul", "pm_workspace_size", "pm_polymul_ws", "pm_shard_bounds"
 # exported by libpolymul_probe.so, in include/polymul_probe.h order
 PROBE_SYMBOLS = ("pm_probe_mac", "pm_probe_oprate", "pm_probe_ops_per_step")
 PROBE_LIB_PATH = os.path.join(HERE, "libpolymul_probe.so")
-OP = {"imad_wide": 0, "imad": 1, "iadd3": 2, "lop3": 3, "shf": 4, "mix": 5}
+OP = {"imad_wide": 0, "imad": 1, "iadd3": 2, "lop3": 3, "shf": 4, "imad_hi": 6}
 
 _lib = None
 

@@ -73,7 +73,9 @@ __global__ void k_probe_mac(u64 iters, u64 seed, u64 *__restrict__ sink)
 // ---------------------------------------------------------------------------
 constexpr int CH = 8;
 
-// 32 x 32 -> 64 multiply-add: x <- lo(x) * b + x
+// 32 x 32 -> 64 multiply-add: x_c <- hi(x_{c+1}) * b + x_c (the multiplicand
+// comes from the next chain's high word, so no register of the product's
+// pair is read and written by the same instruction)
 __global__ void k_rate_imad_wide(u64 iters, u32 seed, u64 *__restrict__ sink, u64 *clk)
 {
     ClockRec cr;
@@ -86,7 +88,7 @@ __global__ void k_rate_imad_wide(u64 iters, u32 seed, u64 *__restrict__ sink, u6
     for (u64 i = 0; i < iters; i++) {
 #pragma unroll
         for (int c = 0; c < CH; c++)
-            asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[c]) : "r"((u32)x[c]), "r"(b));
+            asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(x[c]) : "r"((u32)(x[(c + 1) % CH] >> 32)), "r"(b));
     }
     u64 s = 0;
 #pragma unroll
@@ -189,38 +191,24 @@ __global__ void k_rate_shf(u64 iters, u32 seed, u64 *__restrict__ sink, u64 *clk
     cr.stop();
 }
 
-// The algorithmic mix of one term product: 4 wide multiplies and 14 simple
-// ops (7 three-input adds, 7 three-input logic ops) per step, each on its
-// own chain, so the multiply and ALU pipes can work side by side.
-__global__ void k_rate_mix(u64 iters, u32 seed, u64 *__restrict__ sink, u64 *clk)
+// high half of a 32 x 32 multiply: x <- mulhi(x, b) + x (the add keeps the
+// chain from collapsing to zero)
+__global__ void k_rate_imad_hi(u64 iters, u32 seed, u64 *__restrict__ sink, u64 *clk)
 {
     ClockRec cr;
     cr.start(clk);
     const u32 t = blockIdx.x * blockDim.x + threadIdx.x;
-    u64 w[4];
-    u32 x[7], y[7];
-    const u32 b = seed | 1u, d = seed >> 3;
+    u32 x[CH];
+    const u32 b = seed | 0x80000001u;
 #pragma unroll
-    for (int c = 0; c < 4; c++) w[c] = (u64)(t * 2654435761u + c) << 1;
-#pragma unroll
-    for (int c = 0; c < 7; c++) {
-        x[c] = t * 40503u + c;
-        y[c] = t * 9973u + 3 * c;
-    }
+    for (int c = 0; c < CH; c++) x[c] = t * 2654435761u + c;
     for (u64 i = 0; i < iters; i++) {
 #pragma unroll
-        for (int c = 0; c < 4; c++)
-            asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(w[c]) : "r"((u32)w[c]), "r"(b));
-#pragma unroll
-        for (int c = 0; c < 7; c++) {
-            asm volatile("{ .reg .u32 q; add.u32 q, %0, %1; add.u32 %0, q, %2; }" : "+r"(x[c]) : "r"(x[(c + 1) % 7]),
-                         "r"(d));
-            asm volatile("lop3.b32 %0, %0, %1, %2, 0x96;" : "+r"(y[c]) : "r"(y[(c + 1) % 7]), "r"(d));
-        }
+        for (int c = 0; c < CH; c++) asm volatile("mad.hi.u32 %0, %0, %1, %0;" : "+r"(x[c]) : "r"(b));
     }
-    u64 s = w[0] ^ w[1] ^ w[2] ^ w[3];
+    u32 s = 0;
 #pragma unroll
-    for (int c = 0; c < 7; c++) s ^= x[c] ^ ((u64)y[c] << 32);
+    for (int c = 0; c < CH; c++) s ^= x[c];
     sink[t] = s;
     cr.stop();
 }
@@ -247,7 +235,7 @@ extern "C" int pm_probe_oprate(int op, uint32_t blocks, uint32_t threads, uint64
     case PM_OP_IADD3: pm::k_rate_iadd3<<<blocks, threads, 0, s>>>(iters, seed, k, c); break;
     case PM_OP_LOP3: pm::k_rate_lop3<<<blocks, threads, 0, s>>>(iters, seed, k, c); break;
     case PM_OP_SHF: pm::k_rate_shf<<<blocks, threads, 0, s>>>(iters, seed, k, c); break;
-    case PM_OP_MIX: pm::k_rate_mix<<<blocks, threads, 0, s>>>(iters, seed, k, c); break;
+    case PM_OP_IMAD_HI: pm::k_rate_imad_hi<<<blocks, threads, 0, s>>>(iters, seed, k, c); break;
     default: return PM_EINVAL;
     }
     return cudaGetLastError() == cudaSuccess ? PM_OK : PM_ECUDA;
@@ -260,8 +248,8 @@ extern "C" uint32_t pm_probe_ops_per_step(int op)
     case PM_OP_IMAD:
     case PM_OP_IADD3:
     case PM_OP_LOP3:
-    case PM_OP_SHF: return pm::CH;
-    case PM_OP_MIX: return 18;
+    case PM_OP_SHF:
+    case PM_OP_IMAD_HI: return pm::CH;
     default: return 0;
     }
 }
