@@ -104,6 +104,12 @@ typedef struct pm_terms_out {
 #define PM_STRATEGY_HASH   3  /* hashed windows: a shared-memory hash table per
                                  window of up to 2^32 ranks (sparse results in
                                  large boxes)                                      */
+#define PM_STRATEGY_BUCKET 4  /* every term product written to a bucket of the
+                                 output key space (two passes over the
+                                 pp-matrix), each bucket sorted and reduced in
+                                 shared memory: results about as large as the
+                                 term products (mod p and int128 kinds; takes
+                                 32 or 56 bytes of scratch per term product)    */
 
 /* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
 /* Direct strategy accumulators (mod p kind). */
@@ -145,9 +151,10 @@ typedef struct pm_stats {
     uint64_t n_ranges;         /* output key ranges (one CTA each; hash: windows
                                   run over all rounds)                            */
     uint64_t box;              /* output-exponent box size used for ranks          */
-    int32_t strategy;          /* PM_STRATEGY_DIRECT, _SORT or _HASH              */
+    int32_t strategy;          /* PM_STRATEGY_DIRECT, _SORT, _HASH or _BUCKET     */
     uint32_t refine_rounds;    /* partition refinement rounds (sort); window
-                                  rounds (hash)                                   */
+                                  rounds (hash); buckets sorted outside shared
+                                  memory (bucket)                                 */
     uint32_t kernel_launches;  /* kernels launched by the call                     */
     uint32_t host_syncs;       /* stream synchronisations by the call              */
     float ms_range_kernel;     /* device time of the accumulate kernel alone: one

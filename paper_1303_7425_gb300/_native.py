@@ -20,7 +20,7 @@ PM_MAX_VARS = 16
 PM_OK, PM_EINVAL, PM_EEXP_OVERFLOW, PM_ECOEF_BOUND = 0, -1, -2, -3
 PM_ECAPACITY, PM_ENOMEM, PM_ETIMEOUT, PM_ECUDA, PM_EPLAN, PM_ECANCELED = -4, -5, -6, -7, -8, -9
 KIND = {"m61": 0, "i64": 1, "i192": 2}
-STRATEGY = {"auto": 0, "direct": 1, "sort": 2, "hash": 3}
+STRATEGY = {"auto": 0, "direct": 1, "sort": 2, "hash": 3, "bucket": 4}
 STRATEGY_NAME = {v: k for k, v in STRATEGY.items()}
 ACCUMULATOR = {"auto": 0, "wide": 1, "limbs": 2, "limbs3": 3}
 

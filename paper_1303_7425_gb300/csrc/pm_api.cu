@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "pm_bucket.cuh"
 #include "pm_direct.cuh"
 #include "pm_pack.cuh"
 #include "pm_partition.cuh"
@@ -24,6 +25,10 @@ int out_bound_and_box(const pm_packing *pk, const pm_terms_in *f, const pm_terms
                       cudaStream_t s);
 
 constexpr u32 DEFAULT_CHUNK = 4096;    // sort: term products per range
+// bucket strategy: chosen automatically when its scratch -- a record and a
+// result slot per term product, 32 bytes (mod p) or 56 bytes (int64) --
+// stays within this many bytes
+constexpr u64 BUCKET_MAX_BYTES = 32ull << 30;
 constexpr u32 MAX_CHUNK = 4096;
 
 // ---------------------------------------------------------------------------
@@ -313,7 +318,7 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
     pm_options o;
     memset(&o, 0, sizeof(o));
     if (opt) o = *opt;
-    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 3 || o.accumulator < 0 || o.accumulator > 3 ||
+    if (o.chunk > MAX_CHUNK || o.strategy < 0 || o.strategy > 4 || o.accumulator < 0 || o.accumulator > 3 ||
         o.grid_l > 4096)
         throw Error(PM_EINVAL, "bad options");
     pm_stats stats;
@@ -460,9 +465,14 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
             strategy = PM_STRATEGY_DIRECT;
         else if (box <= 64 * products)
             strategy = PM_STRATEGY_HASH;
+        else if (kind != PM_COEF_I64_ACC192 && products >= (1ull << 20) &&
+                 products <= BUCKET_MAX_BYTES / (kind == PM_COEF_M61 ? 32ull : 56ull))
+            strategy = PM_STRATEGY_BUCKET;  // every product through the buckets
         else
             strategy = PM_STRATEGY_SORT;
     }
+    if (strategy == PM_STRATEGY_BUCKET && kind == PM_COEF_I64_ACC192)
+        throw Error(PM_EINVAL, "the bucket strategy takes the mod p and int128 kinds");
     if (strategy == PM_STRATEGY_DIRECT && box >= (1ull << 40))
         throw Error(PM_EINVAL, "exponent box too large for the direct strategy");
     stats.strategy = strategy;
@@ -540,7 +550,37 @@ static int polymul_impl(const pm_packing *pk, int kind, const pm_terms_in *f, co
         return finish(n_out);
     }
 
-    if (strategy == PM_STRATEGY_DIRECT) {
+    if (strategy == PM_STRATEGY_BUCKET) {
+        // every term product to a bucket of its key, each bucket sorted and
+        // reduced in shared memory (pm_bucket.cu)
+        u64 klo = hs.fl_f[0] + hs.fl_g[0], kend = hs.fl_f[1] + hs.fl_g[1] + 1;
+        if (!ks.whole()) {
+            klo = std::max(klo, ks.lo);
+            kend = std::min(kend, ks.hi);
+        }
+        BucketInputs in;
+        in.A = F.key;
+        in.Ac = F.coef;
+        in.B = G.key;
+        in.Bc = G.coef;
+        in.na = (u32)F.n;
+        in.nb = (u32)G.n;
+        in.A_last = hs.fl_f[1];
+        in.B_last = hs.fl_g[1];
+        if (st) PM_CUDA(cudaEventRecord(e0, c.s));
+        if (st) PM_CUDA(cudaEventRecord(k0, c.s));
+        const BucketSlices bs = bucket_product(c, S, in, kind, klo, kend, products);
+        if (st) PM_CUDA(cudaEventRecord(k1, c.s));
+        if (st) PM_CUDA(cudaEventRecord(e1, c.s));
+        stats.n_ranges = bs.n;
+        stats.refine_rounds = bs.big;
+        okey = bs.key;
+        ocoef = bs.coef;
+        ucount = const_cast<u64 *>(bs.ucount);
+        slice_base = const_cast<u64 *>(bs.base);
+        slice_base0 = 0;
+        nslices = (u32)bs.n;
+    } else if (strategy == PM_STRATEGY_DIRECT) {
         // K-b: ranks, grid sample, groups (no host sync)
         u32 *g32 = S.get<u32>(G.n);
         u32 *f32 = box <= 0xFFFFFFFFull ? S.get<u32>(F.n) : nullptr;

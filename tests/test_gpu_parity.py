@@ -412,3 +412,57 @@ def test_pack_unpack_roundtrip():
     np.testing.assert_array_equal(keys.cpu().numpy().view(np.uint64), pack_np(e, bits))
     back = P.unpack(bits, keys)
     np.testing.assert_array_equal(back.cpu().numpy().view(np.uint32), e)
+
+
+@pytest.mark.parametrize("case", ["sparse5", "sparse3", "sparse8", "i64", "dense_collisions", "hot_keys"])
+def test_bucket_strategy_exact(case):
+    """The bucketed strategy (every term product to a bucket of its key,
+    buckets sorted in shared memory; buckets above the chunk by a device-wide
+    sort): bit-exact with the oracle on sparse products, int64 inputs, dense
+    operands whose products collide on every key, and univariate operands
+    whose middle keys draw more products than a bucket holds."""
+    if case == "sparse5":
+        w = polygen.sparse_product(polygen.Stream(51, 0), 5, 1500, 900)
+    elif case == "sparse3":
+        w = polygen.sparse_product(polygen.Stream(52, 0), 3, 2000, 1700, 300)
+    elif case == "sparse8":
+        w = polygen.sparse_product(polygen.Stream(53, 0), 8, 700, 3000)
+    elif case == "i64":
+        st = polygen.Stream(54, 0)
+        e = polygen.distinct_random_vectors(st, 1200, 4, 4000)
+        g = polygen.distinct_random_vectors(st, 1100, 4, 4000)
+        w = polygen.Workload("b64", 4, [16] * 4, "i64", polygen.Poly(e, st.coef_i64(1200, 1 << 40)),
+                             polygen.Poly(g, st.coef_i64(1100, 1 << 40)))
+    elif case == "dense_collisions":
+        mons = polygen.monomials_total_degree(3, 14)
+        st = polygen.Stream(55, 0)
+        w = polygen.Workload("bd", 3, [12] * 3, "m61", polygen.Poly(mons, st.coef_m61(len(mons))),
+                             polygen.Poly(mons[::-1].copy(), st.coef_m61(len(mons))))
+    else:
+        st = polygen.Stream(56, 0)
+        fe = np.arange(4300, dtype=np.uint32).reshape(-1, 1)
+        w = polygen.Workload("hot", 1, [16], "m61", polygen.Poly(fe, st.coef_m61(4300)),
+                             polygen.Poly(fe[::-1].copy(), st.coef_m61(4300)))
+    ref = _oracle(w)
+    gpu = run_gpu(w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, strategy="bucket")
+    assert gpu[2]["strategy"] == "bucket"
+    if case == "hot_keys":
+        assert gpu[2]["refine_rounds"] > 0          # buckets sorted outside shared memory
+    assert_same(gpu, ref, w.field_bits)
+
+
+def test_bucket_strategy_chosen_for_large_sparse_products():
+    """Sparse products of at least 2^20 term products whose result box is
+    more than 64 times the work take the bucketed strategy by default, and
+    give the sort strategy's result bit for bit."""
+    import paper_1303_7425_gb300 as P
+    w = polygen.sparse_product(polygen.Stream(57, 0), 5, 1500, 1200)
+    gpu = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    assert gpu[2]["strategy"] == "bucket"
+    srt = run_gpu(w.field_bits, "m61", w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, strategy="sort")
+    np.testing.assert_array_equal(gpu[0], srt[0])
+    np.testing.assert_array_equal(gpu[1], srt[1])
+    with pytest.raises(P.PolymulError) as ei:                       # no 192-bit bucket path
+        run_gpu(w.field_bits, "i192", w.f.exps, w.f.coefs.astype(np.int64) >> 4, w.g.exps,
+                w.g.coefs.astype(np.int64) >> 4, strategy="bucket")
+    assert ei.value.code == -1

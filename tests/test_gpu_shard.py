@@ -28,6 +28,7 @@ def _cases():
                                          polygen.Poly(dense.copy(), st.coef_i64(len(dense), 1 << 40))), "auto"),
         "sparse5_sort": (polygen.sparse_product(polygen.Stream(9, 0), 5, 1500, 900, 30), "sort"),
         "sparse3_hash": (polygen.sparse_product(polygen.Stream(12, 0), 3, 2000, 2000, 400), "hash"),
+        "sparse5_bucket": (polygen.sparse_product(polygen.Stream(13, 0), 5, 1500, 900), "bucket"),
     }
 
 
@@ -65,7 +66,7 @@ def test_shards_concatenate_to_the_product(name, nshards):
     np.testing.assert_array_equal(wc.reshape(-1), np.asarray(c, dtype=np.uint64).reshape(-1))
 
 
-@pytest.mark.parametrize("strategy", ["direct", "sort", "hash"])
+@pytest.mark.parametrize("strategy", ["direct", "sort", "hash", "bucket"])
 def test_arbitrary_key_slices(strategy):
     """Bounds drawn at random over the whole 64-bit range and near the
     product's keys, including keys whose fields lie outside the exponent box

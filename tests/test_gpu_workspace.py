@@ -29,6 +29,7 @@ def _cases():
                                dict(strategy="direct")),
         "sparse5_sort": (polygen.sparse_product(polygen.Stream(9, 0), 5, 1500, 900, 30), dict(strategy="sort")),
         "sparse3_hash": (polygen.sparse_product(polygen.Stream(12, 0), 3, 2000, 2000, 400), dict(strategy="hash")),
+        "sparse5_bucket": (polygen.sparse_product(polygen.Stream(13, 0), 5, 1500, 900), dict(strategy="bucket")),
     }
 
 
@@ -76,7 +77,7 @@ def test_workspace_exhausted_at_every_stage_fails_cleanly():
     import torch
 
     import paper_1303_7425_gb300 as P
-    for name in ("sparse4v_auto", "dense4v_direct", "sparse3_hash"):
+    for name in ("sparse4v_auto", "dense4v_direct", "sparse3_hash", "sparse5_bucket"):
         w, opts = _cases()[name]
         f = to_dev(w.f.exps, w.f.coefs, w.kind)
         g = to_dev(w.g.exps, w.g.coefs, w.kind)
