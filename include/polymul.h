@@ -388,6 +388,13 @@ int pm_autotune(const pm_packing *pk, int coef_kind, const pm_terms_in *f, const
  * captured once into a CUDA graph when the plan is created and each run
  * replays that graph.  Every product uses the sort strategy.
  *
+ * Output placement: an item whose h.cap >= n_f * n_g has its ranges written
+ * straight into h, each at the count of its product's term products below
+ * the range, and moved left in place when some term products shared a
+ * monomial; h[h.n, h.cap) then holds unspecified words.  An item with a
+ * smaller h.cap has its ranges written to the plan's workspace and copied
+ * into h once their sizes are known (PM_ECAPACITY when they do not fit).
+ *
  * Limits: n_f, n_g <= PM_BATCH_MAX_TERMS per product (larger products belong
  * to pm_polymul).  A plan keeps device pointers to the items' inputs and
  * outputs: they must stay valid and unmoved while the plan is used; a run

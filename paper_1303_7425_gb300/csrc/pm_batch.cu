@@ -18,9 +18,14 @@
 //   B4  one CTA per product sizes its result, checks the capacity and
 //       places its ranges in ascending order; then warps on all SMs copy
 //       the ranges into the callers' outputs.
-// No two CTAs write the same output term.  Scratch for range results is
-// claimed from a device bump counter, bounded by the products' term
-// products.
+// No two CTAs write the same output term.  A product whose output capacity
+// holds all its term products writes each range's terms straight into h, at
+// the number of term products below the range (the sum of the rows' column
+// cursors at the range's start): when no two products share a monomial --
+// the usual case of sparse supports -- that is the term's final place, and
+// B4 only checks it; otherwise B4 moves the ranges left into place.  Other
+// products claim scratch for their range results from a device bump
+// counter (bounded by their term products) and B4 copies them.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -64,7 +69,7 @@ struct BDesc {
     u64 op_off;   // canonical f at op_off, g at op_off + nf
     u64 rg_off;   // ranges [rg_off, rg_off + rcap)
     u32 rcap;
-    u32 pad0;
+    u32 direct;   // results go straight to h (h.cap >= n_f n_g): see kb_ranges
     // out_
     u32 status;   // ST_* bits
     u32 cf, cg, nranges;
@@ -503,9 +508,16 @@ __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *
 // claim_r being the range's output base as thread 0 holds it.  Returns the
 // terms written.  Ends without a barrier: the caller's next scan separates
 // this piece's reads of the shared buffers from the next piece's writes.
+// Where a range's terms go: the scratch (CW words per term) or, for a
+// direct product, its output (the product's own words per term).
+struct Dest {
+    u64 *key, *coef;
+    u32 words;
+};
+
 template <u32 CW, u32 MAXT>
 __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
-                         u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws)
+                         u64 total, u64 plo, u64 phi, u64 claim_r, u64 written, u64 *s_out, u64 *ws, Dest dst_)
 {
     typedef Rng<CW, MAXT> R;
     const u32 tid = threadIdx.x;
@@ -621,9 +633,9 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
         const u32 i = s0 + 32 * t + lane;
         if ((nzmask[t] >> lane) & 1u) {
             const u64 dst = out + wbase + before + (u32)__popc(nzmask[t] & ((1u << lane) - 1u));
-            a.skey[dst] = m.kA[i];
-            a.scoef[CW * dst] = v0[t];
-            if (CW == 2) a.scoef[2 * dst + 1] = v1[t];
+            dst_.key[dst] = m.kA[i];
+            dst_.coef[dst_.words * dst] = v0[t];
+            if (dst_.words == 2) dst_.coef[2 * dst + 1] = v1[t];
         }
         before += (u32)__popc(nzmask[t]);
     }
@@ -634,7 +646,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
 // products; writes at most one term
 template <u32 CW, u32 MAXT>
 __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
-                          u32 cf, u64 key, u64 out, u64 *ws)
+                          u32 cf, u64 key, u64 out, u64 *ws, Dest dst_)
 {
     const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     u64 s0 = 0, s1 = 0;
@@ -671,9 +683,9 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
         }
         wrote = 0;
         if ((r0w | r1w) != 0) {
-            a.skey[out] = key;
-            a.scoef[CW * out] = r0w;
-            if (CW == 2) a.scoef[2 * out + 1] = r1w;
+            dst_.key[out] = key;
+            dst_.coef[dst_.words * out] = r0w;
+            if (dst_.words == 2) dst_.coef[2 * out + 1] = r1w;
             wrote = 1;
         }
     }
@@ -744,6 +756,16 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                 m.cur[r] = (uint16_t)c;
             }
         }
+        // a direct product's terms below the first range: the sum of the
+        // row cursors (term products with keys below the range's start)
+        const Dest dst_ = d.direct ? Dest{d.hkey, d.hcoef, (int)d.kind == PM_COEF_M61 ? 1u : 2u}
+                                   : Dest{a.skey, a.scoef, CW};
+        u64 omega = 0;
+        if (d.direct) {
+            u64 mine_c = 0;
+            for (u32 r = tid; r < cf; r += RNG_T) mine_c += m.cur[r];
+            block_exclusive_scan(mine_c, omega, ws);
+        }
         __syncthreads();
         for (u32 k = first; k < last; k++) {
             const u64 rlo_k = a.rlo[d.rg_off + k], rhi_k = a.rhi[d.rg_off + k];
@@ -758,15 +780,17 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             u64 tot;
             const u64 base = block_exclusive_scan(mine, tot, ws);
             const u64 O = (u32)tot;
-            // claim the range's output space (at most O terms); only thread
-            // 0 holds the base, and waits for it when a piece publishes it
-            u64 claim_r = 0;
-            if (tid == 0) claim_r = atomicAdd(a.bump, O);
+            // the range's output base: a direct product's term products
+            // below the range; otherwise claimed scratch (at most O terms),
+            // held by thread 0 only and waited for when a piece publishes it
+            u64 claim_r = omega;
+            if (!d.direct && tid == 0) claim_r = atomicAdd(a.bump, O);
+            omega += O;
             u64 written = 0;
             if (O <= R::CHUNK) {
                 if (O) {
                     piece_offsets<CW, MAXT>(m, cf, base, tot);
-                    written = rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws);
+                    written = rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, tot, rlo_k, rhi_k, claim_r, 0, &claim, ws, dst_);
                 }
                 // own rows only: other threads read these cursors after the
                 // next scan
@@ -791,12 +815,13 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                         if (PO <= R::CHUNK) {
                             if (PO) {
                                 piece_offsets<CW, MAXT>(m, cf, pbase, ptot);
-                                written += rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws);
+                                written += rng_piece<CW, MAXT>(a, d, m, A, Ac, Bc, ptot, plo, phi, claim_r, written, &claim, ws,
+                                                               dst_);
                             }
                             break;
                         }
                         if (phi - plo == 1) {
-                            written += rng_single<CW, MAXT>(a, d, m, A, Ac, Bc, cf, plo, claim_r + written, ws);
+                            written += rng_single<CW, MAXT>(a, d, m, A, Ac, Bc, cf, plo, claim_r + written, ws, dst_);
                             break;
                         }
                         phi = plo + (phi - plo) / 2;
@@ -826,6 +851,49 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
 
 constexpr u64 SKIP = ~0ull;
 
+// A direct product whose ranges hold fewer terms than term products (some
+// products shared a monomial): its ranges, written at the term products
+// below them, move left into place in ascending order, one CTA.  Range k's
+// destination [F_k, F_k + u_k) never reaches a later range's source (F_k +
+// u_k = F_{k+1} <= the next range's base), and each chunk is read whole
+// before any of it is written, so the moves are safe in place.
+__device__ void direct_compact(const BArgs &a, BDesc &d, u32 nr)
+{
+    constexpr u32 PER = 4, CH = FIN_T * PER;
+    const u64 *rb = a.rbase + d.rg_off, *rc = a.rcount + d.rg_off;
+    const u32 words = (int)d.kind == PM_COEF_M61 ? 1u : 2u, tid = threadIdx.x;
+    u64 F = 0;
+    for (u32 k = 0; k < nr; k++) {
+        const u64 src = rb[k], n = rc[k];
+        if (src != F) {
+            for (u64 c0 = 0; c0 < n; c0 += CH) {
+                u64 kk[PER], c0w[PER], c1w[PER];
+#pragma unroll
+                for (u32 q = 0; q < PER; q++) {
+                    const u64 t = c0 + q * FIN_T + tid;
+                    if (t < n) {
+                        kk[q] = d.hkey[src + t];
+                        c0w[q] = d.hcoef[words * (src + t)];
+                        c1w[q] = words == 2 ? d.hcoef[2 * (src + t) + 1] : 0;
+                    }
+                }
+                __syncthreads();
+#pragma unroll
+                for (u32 q = 0; q < PER; q++) {
+                    const u64 t = c0 + q * FIN_T + tid;
+                    if (t < n) {
+                        d.hkey[F + t] = kk[q];
+                        d.hcoef[words * (F + t)] = c0w[q];
+                        if (words == 2) d.hcoef[2 * (F + t) + 1] = c1w[q];
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        F += n;
+    }
+}
+
 __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
 {
     __shared__ u64 ws[32];
@@ -840,6 +908,16 @@ __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
         u64 cnt;
         block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
         total += cnt;
+    }
+    if (d.direct) {
+        // the terms are in h already; in place unless monomials repeated
+        if (nr && total != (u64)d.cf * d.cg) direct_compact(a, d, nr);
+        for (u32 k = tid; k < d.rcap; k += FIN_T) {
+            rlo[k] = 0;
+            rhi[k] = SKIP;
+        }
+        if (tid == 0) d.n_out = d.status ? 0 : total;
+        return;
     }
     const bool fits = total <= d.hcap;
     u64 run = 0;
@@ -895,7 +973,7 @@ constexpr size_t CAN_SMEM = (size_t)BT_MAX_TERMS * (8 + 8 + 2 + 2) + (CAN_T / 32
 constexpr size_t PLAN_SMEM = (size_t)PLAN_SAMPLES * (8 + 8 + 2 + 2) + (PLAN_T / 32) * 256 * 4;
 
 struct BatchSizes {
-    u64 op_total = 0, rg_total = 0, prod_total = 0;
+    u64 op_total = 0, rg_total = 0, prod_total = 0, term_total = 0;   // prod_total: scratch terms
     u32 nitems = 0, cw = 1, maxt = 4096, target = 0, per_item = 0;
 };
 
@@ -986,7 +1064,11 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
         d.op_off = z.op_total;
         z.op_total += d.nf + d.ng;
         const u64 P = (u64)d.nf * d.ng;
-        z.prod_total += P;
+        // the output holds every term product: the range kernel writes the
+        // results straight into it, no scratch
+        d.direct = it.h.cap >= P ? 1u : 0u;
+        if (!d.direct) z.prod_total += P;
+        z.term_total += P;
         u64 rcap = P ? (P + z.target - 1) / z.target + 1 : 1;
         if (rcap > PLAN_SAMPLES) rcap = PLAN_SAMPLES;
         d.rcap = (u32)rcap;
@@ -1166,7 +1248,7 @@ static void batch_create(const pm_batch_item *items, uint32_t count, const pm_ba
     PM_CUDA(cudaMemcpyAsync(base + w.ifr, ifr.data(), 4 * (size_t)z.nitems, cudaMemcpyHostToDevice, stream));
     PM_CUDA(cudaStreamSynchronize(stream));
     memset(&pl->stats, 0, sizeof(pl->stats));
-    pl->stats.term_products = z.prod_total;
+    pl->stats.term_products = z.term_total;
     pl->stats.work_items = z.nitems;
     pl->stats.kernel_launches = 4;
     set_batch_smem();

@@ -139,6 +139,32 @@ def test_batch_heavy_multiplicity():
     _check_against_oracle(prods[0], res[0][1])
 
 
+@pytest.mark.parametrize("opts", [dict(), dict(range_target=64, ranges_per_item=1)])
+def test_direct_and_copied_outputs_agree(opts):
+    """The same products twice in one batch: once with h.cap >= n_f n_g
+    (ranges written straight into h, moved left where monomials repeat) and
+    once with h.cap equal to the result's size (ranges copied in from the
+    workspace).  Both equal the oracle; the univariate dense product makes
+    up to 900 term products per monomial, so nearly every range moves."""
+    import paper_1303_7425_gb300 as P
+    st = polygen.Stream(41, 0)
+    e = np.arange(900, dtype=np.uint32).reshape(-1, 1)
+    uni = polygen.Workload("uni", 1, [16], "m61", polygen.Poly(e, st.coef_m61(900)),
+                           polygen.Poly(e[::-1].copy(), st.coef_m61(900)))
+    ws = [uni] + _mixed_workloads(seed=17, count=8)
+    exact = []
+    for w in ws:
+        ex, _ = oracle.mul(w.nvars, w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+        exact.append(max(len(ex), 1))
+    direct = [_product(w) for w in ws]
+    copied = [_product(w, cap=n) for w, n in zip(ws, exact)]
+    res, stats = P.batch_polymul(direct + copied, **opts)
+    assert stats["term_products"] == 2 * sum(w.f.n * w.g.n for w in ws)
+    for pr, (status, n) in zip(direct + copied, res):
+        assert status == 0
+        _check_against_oracle(pr, n)
+
+
 @pytest.mark.parametrize("kind", ["m61", "i64"])
 def test_batch_clustered_keys_take_the_radix_path(kind):
     """Keys clustered inside a range's interval (64 x 64 products packed in a
