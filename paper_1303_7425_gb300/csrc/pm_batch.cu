@@ -23,7 +23,8 @@
 // the number of term products below the range (the sum of the rows' column
 // cursors at the range's start): when no two products share a monomial --
 // the usual case of sparse supports -- that is the term's final place, and
-// B4 only checks it; otherwise B4 moves the ranges left into place.  Other
+// B4 only checks it; otherwise B4 lists the product's output in units of
+// CMP_CH terms and CTAs on all SMs move them left into place (kb_compact).  Other
 // products claim scratch for their range results from a device bump
 // counter (bounded by their term products) and B4 copies them.
 #include <cstring>
@@ -74,6 +75,7 @@ struct BDesc {
     u32 status;   // ST_* bits
     u32 cf, cg, nranges;
     u64 n_out;
+    u64 cmp_base;  // first compaction unit (kb_compact) of a direct product that moves
     u32 maxe[2][PM_MAX_VARS];
     u64 maxabs[2];
 };
@@ -93,6 +95,8 @@ struct BArgs {
     u32 target;                   // term products per range
     u32 per_item;                 // ranges per work item
     u64 rg_total;                 // range slots of the batch
+    u32 *uprod, *uflag;           // compaction units: product, "sources read" flag
+    u32 *ucount;                  // [0] units listed by kb_finish, [1] units taken by kb_compact
 };
 
 // ---------------------------------------------------------------------------
@@ -851,48 +855,16 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
 
 constexpr u64 SKIP = ~0ull;
 
-// A direct product whose ranges hold fewer terms than term products (some
-// products shared a monomial): its ranges, written at the term products
-// below them, move left into place in ascending order, one CTA.  Range k's
-// destination [F_k, F_k + u_k) never reaches a later range's source (F_k +
-// u_k = F_{k+1} <= the next range's base), and each chunk is read whole
-// before any of it is written, so the moves are safe in place.
-__device__ void direct_compact(const BArgs &a, BDesc &d, u32 nr)
-{
-    constexpr u32 PER = 4, CH = FIN_T * PER;
-    const u64 *rb = a.rbase + d.rg_off, *rc = a.rcount + d.rg_off;
-    const u32 words = (int)d.kind == PM_COEF_M61 ? 1u : 2u, tid = threadIdx.x;
-    u64 F = 0;
-    for (u32 k = 0; k < nr; k++) {
-        const u64 src = rb[k], n = rc[k];
-        if (src != F) {
-            for (u64 c0 = 0; c0 < n; c0 += CH) {
-                u64 kk[PER], c0w[PER], c1w[PER];
-#pragma unroll
-                for (u32 q = 0; q < PER; q++) {
-                    const u64 t = c0 + q * FIN_T + tid;
-                    if (t < n) {
-                        kk[q] = d.hkey[src + t];
-                        c0w[q] = d.hcoef[words * (src + t)];
-                        c1w[q] = words == 2 ? d.hcoef[2 * (src + t) + 1] : 0;
-                    }
-                }
-                __syncthreads();
-#pragma unroll
-                for (u32 q = 0; q < PER; q++) {
-                    const u64 t = c0 + q * FIN_T + tid;
-                    if (t < n) {
-                        d.hkey[F + t] = kk[q];
-                        d.hcoef[words * (F + t)] = c0w[q];
-                        if (words == 2) d.hcoef[2 * (F + t) + 1] = c1w[q];
-                    }
-                }
-                __syncthreads();
-            }
-        }
-        F += n;
-    }
-}
+// Compaction units of direct products whose ranges hold fewer terms than
+// term products (some products shared a monomial): unit u covers the
+// output positions [u CMP_CH, (u + 1) CMP_CH), each taken from its range's
+// place Omega_k + (x - F_k) >= x.  A unit reads all its terms, publishes
+// that in its flag, waits for the flags of the units whose sources lie in
+// its destination (earlier units only: sources are never left of their
+// destinations), then writes.
+constexpr int CMP_T = 512;
+constexpr u32 CMP_PER = 8;
+constexpr u32 CMP_CH = CMP_T * CMP_PER;
 
 __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
 {
@@ -910,13 +882,32 @@ __global__ void __launch_bounds__(FIN_T) kb_finish(BArgs a)
         total += cnt;
     }
     if (d.direct) {
-        // the terms are in h already; in place unless monomials repeated
-        if (nr && total != (u64)d.cf * d.cg) direct_compact(a, d, nr);
-        for (u32 k = tid; k < d.rcap; k += FIN_T) {
-            rlo[k] = 0;
-            rhi[k] = SKIP;
+        // the terms are in h already; in place unless monomials repeated,
+        // else the ranges' destinations (rlo) and the compaction units
+        __shared__ u64 s_base;
+        const bool moves = nr && total != (u64)d.cf * d.cg;
+        u64 run = 0;
+        for (u32 k0 = 0; k0 < d.rcap; k0 += FIN_T) {
+            const u32 k = k0 + tid;
+            u64 cnt;
+            const u64 at = run + block_exclusive_scan(k < nr ? rc[k] : 0, cnt, ws);
+            if (k < d.rcap) {
+                rlo[k] = moves && k < nr ? at : 0;
+                rhi[k] = SKIP;
+            }
+            run += cnt;
         }
-        if (tid == 0) d.n_out = d.status ? 0 : total;
+        const u64 units = moves ? (total + CMP_CH - 1) / CMP_CH : 0;
+        if (tid == 0) {
+            d.n_out = d.status ? 0 : total;
+            s_base = units ? atomicAdd(&a.ucount[0], (u32)units) : 0;
+            d.cmp_base = s_base;
+        }
+        __syncthreads();
+        for (u64 i = tid; i < units; i += FIN_T) {
+            a.uprod[s_base + i] = p;
+            a.uflag[s_base + i] = 0;
+        }
         return;
     }
     const bool fits = total <= d.hcap;
@@ -959,6 +950,131 @@ __global__ void __launch_bounds__(256) kb_copy(BArgs a)
     }
 }
 
+__device__ __forceinline__ u32 ld_acquire_u32(const u32 *p)
+{
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(u32 *p, u32 v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// last k in [0, n) with v(k) <= x (v ascending, v(0) <= x), by one warp:
+// each round the 32 lanes probe 32 evenly spaced points
+template <class V>
+__device__ __forceinline__ u32 warp_last_le(V v, u32 n, u64 x)
+{
+    const u32 lane = threadIdx.x & 31;
+    u32 a0 = 0;
+    while (n > 1) {
+        const u32 step = (n + 31) >> 5;
+        const bool le = lane * step < n && v(a0 + lane * step) <= x;
+        const u32 k = 31 - __clz(__ballot_sync(0xffffffffu, le));
+        a0 += k * step;
+        n = min(step, n - k * step);
+    }
+    return a0;
+}
+
+// B4c (all SMs): the compaction units, taken in list order from a counter.
+// A unit only waits for units listed before it, which were taken earlier by
+// running CTAs and publish their reads without waiting, so every wait ends;
+// a wait still bounded, past which the product fails with ST_INTERNAL.
+__global__ void __launch_bounds__(CMP_T) kb_compact(BArgs a)
+{
+    __shared__ u32 s_g, s_fail;
+    __shared__ u32 s_k0, s_ulo, s_ident;
+    const u32 tid = threadIdx.x, lane = tid & 31;
+    for (;;) {
+        if (tid == 0) {
+            s_g = atomicAdd(&a.ucount[1], 1u);
+            s_fail = 0;
+        }
+        __syncthreads();
+        const u32 g = s_g;
+        if (g >= *(volatile u32 *)&a.ucount[0]) break;
+        const u32 p = a.uprod[g];
+        BDesc &d = a.D[p];
+        const u32 nr = d.nranges;
+        const u64 *F = a.rlo + d.rg_off, *Om = a.rbase + d.rg_off, *rc = a.rcount + d.rg_off;
+        const u64 u = g - d.cmp_base, x0 = u * CMP_CH, x1 = min(x0 + CMP_CH, d.n_out);
+        const u32 words = (int)d.kind == PM_COEF_M61 ? 1u : 2u;
+        if (tid < 32) {
+            auto Fv = [&](u32 k) { return F[k]; };
+            auto Ev = [&](u32 k) { return Om[k] + rc[k]; };
+            const u32 k0 = warp_last_le(Fv, nr, x0), k1 = warp_last_le(Fv, nr, x1 - 1);
+            // the smallest destination whose source reaches x0 (range j, the
+            // first whose sources end above x0): its unit is the first one
+            // to wait for
+            const u32 j = Ev(0) > x0 ? 0u : warp_last_le(Ev, nr, x0) + 1;
+            if (lane == 0) {
+                s_k0 = k0;
+                // Omega_k - F_k never decreases with k: the unit stays in
+                // place when its last range does
+                s_ident = Om[k1] == F[k1];
+                s_ulo = j < nr ? (u32)((F[j] + (x0 > Om[j] ? x0 - Om[j] : 0)) / CMP_CH) : (u32)u;
+            }
+        }
+        __syncthreads();
+        if (s_ident) {
+            if (tid == 0) st_release_u32(&a.uflag[g], 1u);
+            __syncthreads();
+            continue;
+        }
+        // read: position x of range k (last k with F_k <= x) comes from
+        // Omega_k + x - F_k
+        u64 kk[CMP_PER], c0[CMP_PER], c1[CMP_PER];
+        u32 k = s_k0;
+#pragma unroll
+        for (u32 q = 0; q < CMP_PER; q++) {
+            const u64 x = x0 + q * CMP_T + tid;
+            if (x < x1) {
+                while (k + 1 < nr && F[k + 1] <= x) k++;
+                const u64 src = Om[k] + (x - F[k]);
+                kk[q] = d.hkey[src];
+                c0[q] = d.hcoef[words * src];
+                c1[q] = words == 2 ? d.hcoef[2 * src + 1] : 0;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            st_release_u32(&a.uflag[g], 1u);
+        }
+        // wait for the earlier units whose sources this unit overwrites
+        const u32 ulo = s_ulo;
+        for (u32 w = ulo + tid; w < (u32)u; w += CMP_T) {
+            const u32 *f = &a.uflag[d.cmp_base + w];
+            u32 spins = 0;
+            while (!ld_acquire_u32(f)) {
+                if (++spins > (1u << 22)) {
+                    atomicOr(&s_fail, 1u);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __syncthreads();
+        if (s_fail) {
+            if (tid == 0) atomicOr(&d.status, ST_INTERNAL);
+        } else {
+#pragma unroll
+            for (u32 q = 0; q < CMP_PER; q++) {
+                const u64 x = x0 + q * CMP_T + tid;
+                if (x < x1) {
+                    d.hkey[x] = kk[q];
+                    d.hcoef[words * x] = c0[q];
+                    if (words == 2) d.hcoef[2 * x + 1] = c1[q];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host: layout, enqueue, plans (graph), workspace mode
 // ---------------------------------------------------------------------------
@@ -974,6 +1090,7 @@ constexpr size_t PLAN_SMEM = (size_t)PLAN_SAMPLES * (8 + 8 + 2 + 2) + (PLAN_T / 
 
 struct BatchSizes {
     u64 op_total = 0, rg_total = 0, prod_total = 0, term_total = 0;   // prod_total: scratch terms
+    u64 unit_total = 0;           // compaction units the direct products may need
     u32 nitems = 0, cw = 1, maxt = 4096, target = 0, per_item = 0;
 };
 
@@ -981,7 +1098,7 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // device workspace layout (every region 256-byte aligned)
 struct WsLayout {
-    size_t D, ck, cc, rlo, rhi, rbase, rcount, ip, ifr, work, bump, skey, scoef, total;
+    size_t D, ck, cc, rlo, rhi, rbase, rcount, ip, ifr, work, bump, skey, scoef, uprod, uflag, ucount, total;
     WsLayout(u32 count, const BatchSizes &z)
     {
         size_t o = 0;
@@ -1003,6 +1120,9 @@ struct WsLayout {
         bump = take(8);
         skey = take(8 * (z.prod_total + 1));
         scoef = take(8 * (size_t)z.cw * (z.prod_total + 1));
+        uprod = take(4 * z.unit_total);
+        uflag = take(4 * z.unit_total);
+        ucount = take(8);
         total = o;
     }
 };
@@ -1068,6 +1188,7 @@ static BatchSizes build_batch(const pm_batch_item *items, u32 count, const pm_ba
         // results straight into it, no scratch
         d.direct = it.h.cap >= P ? 1u : 0u;
         if (!d.direct) z.prod_total += P;
+        else z.unit_total += (P + CMP_CH - 1) / CMP_CH;
         z.term_total += P;
         u64 rcap = P ? (P + z.target - 1) / z.target + 1 : 1;
         if (rcap > PLAN_SAMPLES) rcap = PLAN_SAMPLES;
@@ -1111,6 +1232,9 @@ static BArgs carve_ws(unsigned char *base, u32 count, const BatchSizes &z)
     a.target = z.target;
     a.per_item = z.per_item;
     a.rg_total = z.rg_total;
+    a.uprod = (u32 *)(base + w.uprod);
+    a.uflag = (u32 *)(base + w.uflag);
+    a.ucount = (u32 *)(base + w.ucount);
     return a;
 }
 
@@ -1150,11 +1274,12 @@ static void launch_ranges(const BArgs &a, int sm_count, cudaStream_t s)
     kb_ranges<CW, MAXT><<<sm_count * RNG_CTAS, RNG_T, Rng<CW, MAXT>::SMEM, s>>>(a);
 }
 
-// the four kernels of the pass (counters cleared first)
+// the six kernels of the pass (counters cleared first)
 static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
 {
     PM_CUDA(cudaMemsetAsync(a.work, 0, sizeof(u32), s));
     PM_CUDA(cudaMemsetAsync(a.bump, 0, sizeof(u64), s));
+    PM_CUDA(cudaMemsetAsync(a.ucount, 0, 2 * sizeof(u32), s));
     kb_canon<<<2 * a.count, CAN_T, CAN_SMEM, s>>>(a);
     PM_CUDA(cudaGetLastError());
     kb_plan<<<a.count, PLAN_T, PLAN_SMEM, s>>>(a);
@@ -1171,6 +1296,8 @@ static void launch_pass(const BArgs &a, int sm_count, cudaStream_t s)
     kb_finish<<<a.count, FIN_T, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());
     kb_copy<<<sm_count * 8, 256, 0, s>>>(a);
+    PM_CUDA(cudaGetLastError());
+    kb_compact<<<sm_count * 2, CMP_T, 0, s>>>(a);
     PM_CUDA(cudaGetLastError());
 }
 
@@ -1250,7 +1377,7 @@ static void batch_create(const pm_batch_item *items, uint32_t count, const pm_ba
     memset(&pl->stats, 0, sizeof(pl->stats));
     pl->stats.term_products = z.term_total;
     pl->stats.work_items = z.nitems;
-    pl->stats.kernel_launches = 4;
+    pl->stats.kernel_launches = 6;
     set_batch_smem();
     const int sms = device_sms();
     // capture the whole pass once; runs replay it

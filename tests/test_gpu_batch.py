@@ -166,6 +166,36 @@ def test_direct_and_copied_outputs_agree(opts):
 
 
 @pytest.mark.parametrize("kind", ["m61", "i64"])
+def test_direct_outputs_moved_by_many_units(kind):
+    """A large sparse product with two repeated monomials near the bottom of
+    the key order: nearly its whole output moves left by one or two terms,
+    unit after unit, each unit's destination overlapping the sources of the
+    one before it.  Small ranges make each unit span several."""
+    import paper_1303_7425_gb300 as P
+    base = polygen.sparse_product(polygen.Stream(57, 0), 3, 2500, 2400)
+    fe, ge = base.f.exps.copy(), base.g.exps.copy()
+    # x^0 and x_3 in both operands: x_3 arises twice; x_2 x_3 likewise
+    fe[0], fe[1], fe[2] = (0, 0, 0), (0, 0, 1), (0, 1, 0)
+    ge[0], ge[1], ge[2] = (0, 0, 0), (0, 0, 1), (0, 1, 1)
+    assert len({tuple(r) for r in fe}) == len(fe) and len({tuple(r) for r in ge}) == len(ge)
+    st = polygen.Stream(58, 0)
+    if kind == "m61":
+        fc, gc = st.coef_m61(len(fe)), st.coef_m61(len(ge))
+    else:
+        fc, gc = st.coef_i64(len(fe), 1 << 40), st.coef_i64(len(ge), 1 << 40)
+    w = polygen.Workload("moves", 3, base.field_bits, kind, polygen.Poly(fe, fc), polygen.Poly(ge, gc))
+    e, c = oracle.mul(w.nvars, w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs)
+    keys, coefs = pack_np(e, w.field_bits), np.asarray(c, dtype=np.uint64).reshape(-1)
+    assert len(e) == w.f.n * w.g.n - 2
+    for opts in (dict(range_target=64, ranges_per_item=4), dict()):
+        prods = [_product(w)]
+        res, stats = P.batch_polymul(prods, **opts)
+        assert res[0] == (0, len(e))
+        np.testing.assert_array_equal(prods[0]["out"][0][:len(e)].cpu().numpy().view(np.uint64), keys)
+        np.testing.assert_array_equal(prods[0]["out"][1][:len(e)].cpu().numpy().view(np.uint64).reshape(-1), coefs)
+
+
+@pytest.mark.parametrize("kind", ["m61", "i64"])
 def test_batch_clustered_keys_take_the_radix_path(kind):
     """Keys clustered inside a range's interval (64 x 64 products packed in a
     small corner of a span of about 2^52) put more than 32 pairs into one
