@@ -41,9 +41,6 @@ constexpr int CAN_T = 1024;                       // B1 threads
 constexpr int CAN_IPT = 8;                        // 8192 items
 constexpr int PLAN_T = 1024;                      // B2 threads
 constexpr u32 PLAN_SAMPLES = 8192;
-constexpr int RNG_T = 512;                        // B3 threads
-constexpr u32 RNG_W = RNG_T / 32;
-constexpr int RNG_CTAS = 1;                        // B3 CTAs per SM
 // Products sorted per piece.  A product takes 8 + 8 (keys) + 2 + 2
 // (indexes) + 8 per coefficient word bytes of shared memory, so a batch
 // whose products are all mod p (one word) fits 4096, the others 3072.
@@ -360,15 +357,20 @@ struct RngSmem {
 // gives each thread's starts; rng_piece's first barrier publishes them.
 template <u32 CW, u32 MAXT>
 struct Rng {
+    // threads: 1024 where the shared memory has room for the radix
+    // fallback's per-warp histograms (operands of at most 4096 terms), else
+    // 512; one CTA per SM either way
+    static constexpr int T = MAXT <= 4096 ? 1024 : 512;
+    static constexpr u32 W = T / 32;
     static constexpr u32 CHUNK = rng_chunk(CW);
-    static constexpr int IPT = CHUNK / RNG_T;
-    static constexpr u32 LANE_MAX = (CHUNK / RNG_W + 31) / 32;  // products per lane of a piece
+    static constexpr int IPT = CHUNK / T;
+    static constexpr u32 LANE_MAX = (CHUNK / W + 31) / 32;  // products per lane of a piece
     static constexpr u32 CROW = CHUNK + 8;
-    static constexpr u32 HIST_WORDS = (RNG_T / 32) * 256 > BUCKETS ? (RNG_T / 32) * 256 : BUCKETS;
+    static constexpr u32 HIST_WORDS = (T / 32) * 256 > BUCKETS ? (T / 32) * 256 : BUCKETS;
     static constexpr size_t SMEM = (size_t)MAXT * 8 + MAXT * 2 * 2 +
                                    (size_t)CHUNK * (8 + 8 + 2 + 2 + 8 * CW) + (size_t)HIST_WORDS * 4;
     static_assert((CROW + CHUNK) * 2 <= CHUNK * 8, "row tables overflow the second key buffer");
-    static_assert(CHUNK <= 65535 && CHUNK % RNG_T == 0, "16-bit product offsets, whole sort items per thread");
+    static_assert(CHUNK <= 65535 && CHUNK % T == 0, "16-bit product offsets, whole sort items per thread");
 
     static __device__ __forceinline__ RngSmem carve(unsigned char *p)
     {
@@ -394,9 +396,10 @@ __device__ __forceinline__ u64 row_counts(u32 cnt) { return (u64)cnt | ((u64)(cn
 template <u32 CW, u32 MAXT>
 __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 cf, u64 base, u64 total)
 {
-    uint16_t *coff = (uint16_t *)m.kB, *crow = coff + Rng<CW, MAXT>::CROW;
+    typedef Rng<CW, MAXT> R;
+    uint16_t *coff = (uint16_t *)m.kB, *crow = coff + R::CROW;
     u32 pb = (u32)base, cb = (u32)(base >> 32);
-    for (u32 r = threadIdx.x; r < cf; r += RNG_T) {
+    for (u32 r = threadIdx.x; r < cf; r += R::T) {
         const u32 cnt = (u32)m.ce[r] - m.cur[r];
         if (cnt) {
             coff[cb] = (uint16_t)pb;
@@ -406,7 +409,7 @@ __device__ __forceinline__ void piece_offsets(RngSmem &m, u32 cf, u64 base, u64 
         }
     }
     if (threadIdx.x == 0) coff[total >> 32] = (uint16_t)total;
-    for (u32 x = threadIdx.x; x < BUCKETS; x += RNG_T) m.hist[x] = 0;
+    for (u32 x = threadIdx.x; x < BUCKETS; x += R::T) m.hist[x] = 0;
 }
 
 // Sorts the piece's n (key, index) pairs in kA/iA by key, the bucket counts
@@ -423,8 +426,8 @@ template <u32 CW, u32 MAXT>
 __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *ws)
 {
     typedef Rng<CW, MAXT> R;
-    constexpr u32 PER = BUCKETS / RNG_T;
-    static_assert(BUCKETS % RNG_T == 0, "buckets per thread");
+    constexpr u32 PER = BUCKETS / R::T;
+    static_assert(BUCKETS % R::T == 0, "buckets per thread");
     __shared__ u32 s_bmax;
     const u32 tid = threadIdx.x;
     if (tid == 0) s_bmax = 0;
@@ -447,12 +450,12 @@ __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *
     }
     __syncthreads();
     if (s_bmax > BUCKET_RANK_MAX) {
-        block_sort_pairs<RNG_T, R::IPT>(m.kA, m.iA, m.kB, m.iB, n, varying_bits(lo, lo + span), m.hist, ws);
+        block_sort_pairs<R::T, R::IPT>(m.kA, m.iA, m.kB, m.iB, n, varying_bits(lo, lo + span), m.hist, ws);
         return;
     }
     // scatter by bucket; afterwards hist[b] is the end of bucket b
     if (shift > 0) {
-        for (u32 q = tid; q < n; q += RNG_T) {
+        for (u32 q = tid; q < n; q += R::T) {
             const u64 key = m.kA[q];
             const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
             const u32 p = atomicAdd(&m.hist[b], 1u);
@@ -463,7 +466,7 @@ __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *
         // one key value per bucket, often repeated: one atomic per distinct
         // bucket of a warp
         const u32 lane = tid & 31, nround = (n + 31u) & ~31u;
-        for (u32 i = tid & ~31u; i < nround; i += RNG_T) {
+        for (u32 i = tid & ~31u; i < nround; i += R::T) {
             const u32 q = i + lane;
             const bool valid = q < n;
             const u64 key = valid ? m.kA[q] : 0;
@@ -491,7 +494,7 @@ __device__ void sort_piece(RngSmem &m, u32 n, u64 lo, u64 span, int shift, u64 *
         return;
     }
     // rank inside the bucket, written back to the A buffers
-    for (u32 x = tid; x < n; x += RNG_T) {
+    for (u32 x = tid; x < n; x += R::T) {
         const u64 key = m.kB[x];
         const u32 b = (u32)min((key - lo) >> shift, (u64)BUCKETS - 1);
         const u32 beg = b ? m.hist[b - 1] : 0u, end = m.hist[b];
@@ -539,7 +542,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     // so the global-load latency is paid once per piece.
     const u32 lane = tid & 31, w = tid >> 5;
     {
-        const u32 per_warp = ((O + RNG_W - 1) / RNG_W + 31u) & ~31u;
+        const u32 per_warp = ((O + R::W - 1) / R::W + 31u) & ~31u;
         const u32 p0 = w * per_warp, p1 = min(p0 + per_warp, O);
         u32 rr[R::LANE_MAX], jj[R::LANE_MAX];
         const u32 q0 = p0 + lane;
@@ -600,7 +603,7 @@ __device__ u64 rng_piece(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *
     // segmented reduction: warp w owns the run heads in a contiguous
     // segment of the sorted pairs (a run may continue past it); positions
     // come from ballots and one block scan over the warps' counts
-    const u32 seg = ((n + RNG_W - 1) / RNG_W + 31u) & ~31u;
+    const u32 seg = ((n + R::W - 1) / R::W + 31u) & ~31u;
     const u32 s0 = w * seg, s1 = min(s0 + seg, n);
     u64 v0[R::LANE_MAX], v1[R::LANE_MAX];
     u32 nzmask[R::LANE_MAX];
@@ -652,9 +655,10 @@ template <u32 CW, u32 MAXT>
 __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 *A, const u64 *Ac, const u64 *Bc,
                           u32 cf, u64 key, u64 out, u64 *ws, Dest dst_)
 {
+    typedef Rng<CW, MAXT> R;
     const bool m61 = CW == 1 || (int)d.kind == PM_COEF_M61;
     u64 s0 = 0, s1 = 0;
-    for (u32 r = threadIdx.x; r < cf; r += RNG_T)
+    for (u32 r = threadIdx.x; r < cf; r += R::T)
         for (u32 j = m.cur[r]; j < m.ce[r]; j++) {
             if (m61) {
                 s0 = m61_add(s0, m61_reduce(m61_mul_lazy(Ac[r], Bc[j])));
@@ -665,7 +669,7 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
             }
         }
     // block reduction through the scan helper, word by word with carries
-    __shared__ u64 red[2 * (RNG_T / 32)];
+    __shared__ u64 red[2 * (R::T / 32)];
     const u32 lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int dd = 16; dd > 0; dd >>= 1) {
@@ -681,7 +685,7 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
     __shared__ u64 wrote;
     if (threadIdx.x == 0) {
         u64 r0w = 0, r1w = 0;
-        for (int ww = 0; ww < RNG_T / 32; ww++) {
+        for (int ww = 0; ww < R::T / 32; ww++) {
             if (m61) r0w = m61_add(r0w, red[2 * ww]);
             else add128(r0w, r1w, red[2 * ww], red[2 * ww + 1]);
         }
@@ -698,7 +702,7 @@ __device__ u64 rng_single(const BArgs &a, const BDesc &d, RngSmem &m, const u64 
 }
 
 template <u32 CW, u32 MAXT>
-__global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
+__global__ void __launch_bounds__(Rng<CW, MAXT>::T, 1) kb_ranges(BArgs a)
 {
     typedef Rng<CW, MAXT> R;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -728,19 +732,19 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
         // g's keys in shared memory when they fit, else read through L1
         m.Bs = (u64 *)smem;
         if (cg <= MAXT) {
-            for (u32 j = tid; j < cg; j += RNG_T) m.Bs[j] = Bg[j];
+            for (u32 j = tid; j < cg; j += R::T) m.Bs[j] = Bg[j];
         } else {
             m.Bs = const_cast<u64 *>(Bg);
         }
         __syncthreads();
-        // rows of this thread: tid, tid + RNG_T, ... (neighbouring lanes on
+        // rows of this thread: tid, tid + R::T, ... (neighbouring lanes on
         // neighbouring rows: coalesced row loads, conflict-free cursors); a
         // piece's compacted row table lists them thread by thread, which the
         // generation and the sort do not mind.  Cursors at the first range's
         // start.
         {
             const u64 lo = a.rlo[d.rg_off + first];
-            for (u32 r = tid; r < cf; r += RNG_T) {
+            for (u32 r = tid; r < cf; r += R::T) {
                 const u64 ar = A[r];
                 u32 c = 0;
                 if (lo > ar) {
@@ -767,7 +771,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
         u64 omega = 0;
         if (d.direct) {
             u64 mine_c = 0;
-            for (u32 r = tid; r < cf; r += RNG_T) mine_c += m.cur[r];
+            for (u32 r = tid; r < cf; r += R::T) mine_c += m.cur[r];
             block_exclusive_scan(mine_c, omega, ws);
         }
         __syncthreads();
@@ -775,7 +779,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
             const u64 rlo_k = a.rlo[d.rg_off + k], rhi_k = a.rhi[d.rg_off + k];
             // edges at the range end and the range's product count
             u64 mine = 0;
-            for (u32 r = tid; r < cf; r += RNG_T) {
+            for (u32 r = tid; r < cf; r += R::T) {
                 const u64 ar = A[r];
                 const u32 e = rhi_k > ar ? gallop_up(m.Bs, cg, m.cur[r], rhi_k - ar) : m.cur[r];
                 m.ce[r] = (uint16_t)e;
@@ -798,7 +802,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                 }
                 // own rows only: other threads read these cursors after the
                 // next scan
-                for (u32 r = tid; r < cf; r += RNG_T) m.cur[r] = m.ce[r];
+                for (u32 r = tid; r < cf; r += R::T) m.cur[r] = m.ce[r];
             } else {
                 // bisect by key: pieces [plo, phi) with at most CHUNK
                 // products, or a single monomial
@@ -807,7 +811,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                     u64 phi = rhi_k;
                     for (;;) {
                         u64 cnt_mine = 0;
-                        for (u32 r = tid; r < cf; r += RNG_T) {
+                        for (u32 r = tid; r < cf; r += R::T) {
                             const u64 ar = A[r];
                             const u32 e = phi > ar ? gallop_up(m.Bs, cg, m.cur[r], phi - ar) : m.cur[r];
                             m.ce[r] = (uint16_t)e;
@@ -830,7 +834,7 @@ __global__ void __launch_bounds__(RNG_T, RNG_CTAS) kb_ranges(BArgs a)
                         }
                         phi = plo + (phi - plo) / 2;
                     }
-                    for (u32 r = tid; r < cf; r += RNG_T) m.cur[r] = m.ce[r];
+                    for (u32 r = tid; r < cf; r += R::T) m.cur[r] = m.ce[r];
                     plo = phi;
                 }
             }
@@ -1271,7 +1275,7 @@ static void set_batch_smem()
 template <u32 CW, u32 MAXT>
 static void launch_ranges(const BArgs &a, int sm_count, cudaStream_t s)
 {
-    kb_ranges<CW, MAXT><<<sm_count * RNG_CTAS, RNG_T, Rng<CW, MAXT>::SMEM, s>>>(a);
+    kb_ranges<CW, MAXT><<<sm_count, Rng<CW, MAXT>::T, Rng<CW, MAXT>::SMEM, s>>>(a);
 }
 
 // the six kernels of the pass (counters cleared first)
