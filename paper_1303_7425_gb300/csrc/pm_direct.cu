@@ -115,6 +115,24 @@ __device__ __forceinline__ u32 walk_down(const K *B, u32 j, u64 x)
     return lo + lower_bound_k(B + lo, hi - lo, x);
 }
 
+// first index j' >= j with a[j'] >= x (n if none), a sorted: doubling steps
+// from j, then a binary search of the last step
+template <class K>
+__device__ __forceinline__ u32 gallop_up_k(const K *a, u32 n, u32 j, u64 x)
+{
+    if (j >= n || (u64)a[j] >= x) return j;
+    u32 lo = j, step = 1;  // a[lo] < x
+    for (;;) {
+        const u32 probe = lo + step;
+        if (probe >= n || (u64)a[probe] >= x) {
+            const u32 top = probe < n ? probe : n;
+            return lo + 1 + lower_bound_k(a + lo + 1, top - lo - 1, x);
+        }
+        lo = probe;
+        step <<= 1;
+    }
+}
+
 // first index in [0, n) with a[i] >= x (n if none), by one warp: each round
 // the 32 lanes probe 32 evenly spaced points of the interval that holds the
 // answer, and the ballot of the probes below x narrows it 32-fold (three
@@ -1162,10 +1180,12 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 // staging per window explode.  Here a window may span up to 2^31 ranks; its
 // distinct result monomials go to a shared-memory hash table (HT slots,
 // linear probing, bounded), and FindEdge is done inside the kernel: for the
-// window's two boundaries each thread walks a staircase over a contiguous
-// chunk of rows (the row edges fall as the row rises, Sec. 2) and leaves the
-// column range of every row in a per-CTA scratch; then each thread inserts
-// the products of rows tid, tid + 1024, ... directly.  Emission sorts the
+// window's two boundaries every row's column edges move up from where the
+// CTA's previous window left them (a CTA takes runs of consecutive windows
+// and the windows ascend, so the edges only rise, Sec. 2) by a short gallop
+// per row, the rows independent of one another; rows new to the CTA start
+// from column 0.  Each thread then inserts the products of its rows (tid,
+// tid + 1024, ...) directly.  Emission sorts the
 // occupied slots by rank (block_sort_interval) and writes the window's
 // terms in order.  A window with more than HT_LOAD distinct monomials (or a
 // probe run longer than HT_PROBES) is abandoned and reported; the host
@@ -1173,6 +1193,7 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 // ---------------------------------------------------------------------------
 
 constexpr u32 HT = 4096, HT_BITS = 12;
+constexpr u32 HWIN_RUN = 8;   // consecutive windows a CTA takes at a time
 constexpr u32 HT_LOAD = 3072;
 constexpr u32 HT_PROBES = 64;
 constexpr u32 HEMPTY = 0xFFFFFFFFu;
@@ -1184,7 +1205,7 @@ struct HashArgs {
     u32 na, nb;
     const u64 *wlo, *whi;        // the round's windows (rank bounds)
     u32 nwin;
-    u32 *E2;                     // per CTA: column ranges of the window's rows, 2 * na words
+    u32 *E2;                     // per CTA: column ranges of rows in its last window, 2 * na words (by row)
     u64 *okey, *ocoef;           // window w's terms at w * HT (coefficient words: words)
     u64 *ucount;                 // terms of window w, or HFAILED
     u32 *wnext;                  // window counter
@@ -1215,42 +1236,40 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         keys[x] = HEMPTY;
         acc.zero(x);
     }
+    if (tid == 0) {
+        s_rows[0] = 0;
+        s_rows[1] = 0;
+    }
+    u32 pi1 = 0;   // rows below pi1 hold edges of an earlier window of this CTA
     for (;;) {
-        if (tid == 0) {
-            s_next = atomicAdd(a.wnext, 1u);
-            s_count = 0;
-            s_over = 0;
-        }
+        if (tid == 0) s_next = atomicAdd(a.wnext, HWIN_RUN);
         __syncthreads();
-        const u32 wk = s_next;
-        if (wk >= a.nwin) break;
+        const u32 wbase = s_next;
+        if (wbase >= a.nwin) break;
+        const u32 wstop = min(wbase + HWIN_RUN, a.nwin);
+        for (u32 wk = wbase; wk < wstop; wk++) {
         const u64 lo = a.wlo[wk], hi = a.whi[wk];
         const u32 span = (u32)(hi - lo);
         if (tid == 0) {
-            s_rows[0] = lo > bmax ? lower_bound_k(a.A, a.na, lo - bmax) : 0u;
-            s_rows[1] = hi > bmin ? lower_bound_k(a.A, a.na, hi - bmin) : 0u;
+            s_count = 0;
+            s_over = 0;
+            // rows reaching the window, from the last window's rows
+            s_rows[0] = lo > bmax ? gallop_up_k(a.A, a.na, s_rows[0], lo - bmax) : s_rows[0];
+            s_rows[1] = hi > bmin ? gallop_up_k(a.A, a.na, s_rows[1], hi - bmin) : s_rows[1];
         }
         __syncthreads();
         const u32 i0 = s_rows[0], i1 = s_rows[1];
-        // FindEdge for both boundaries: a staircase per thread chunk
-        {
-            const u32 per = (i1 - i0 + DT - 1) / DT;
-            const u32 r0 = i0 + tid * per, r1 = min(r0 + per, i1);
-            if (r0 < r1) {
-                u64 ar = a.A[r0];
-                u32 jl = lower_bound_k(a.B, a.nb, lo > ar ? lo - ar : 0);
-                u32 jh = lower_bound_k(a.B, a.nb, hi > ar ? hi - ar : 0);
-                E2[2 * (r0 - i0)] = jl;
-                E2[2 * (r0 - i0) + 1] = jh;
-                for (u32 r = r0 + 1; r < r1; r++) {
-                    ar = a.A[r];
-                    jl = walk_down(a.B, jl, lo > ar ? lo - ar : 0);
-                    jh = walk_down(a.B, jh, hi > ar ? hi - ar : 0);
-                    E2[2 * (r - i0)] = jl;
-                    E2[2 * (r - i0) + 1] = jh;
-                }
-            }
+        // FindEdge for both boundaries: each row's edges rise from its edge
+        // at the last window's top (0 for rows new to this CTA)
+        for (u32 r = i0 + tid; r < i1; r += DT) {
+            const u64 ar = a.A[r];
+            const u32 js = r < pi1 ? E2[2 * r + 1] : 0u;
+            const u32 jl = gallop_up_k(a.B, a.nb, js, lo > ar ? lo - ar : 0);
+            const u32 jh = gallop_up_k(a.B, a.nb, js, hi > ar ? hi - ar : 0);
+            E2[2 * r] = jl;
+            E2[2 * r + 1] = jh;
         }
+        if (i1 > pi1) pi1 = i1;
         __syncthreads();
         // the products: each thread takes rows i0 + tid, i0 + tid + DT, ...
         // and inserts its row's products (a window in a sparse box has few
@@ -1259,7 +1278,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         const volatile u32 *over = &s_over;
         for (u32 i = i0 + tid; i < i1; i += DT) {
             if (*over) break;
-            const u32 jl = E2[2 * (i - i0)], jh = E2[2 * (i - i0) + 1];
+            const u32 jl = E2[2 * i], jh = E2[2 * i + 1];
             if (jh <= jl) continue;
             const u32 ra = (u32)a.A[i] - (u32)lo;
             const u64 ca = a.Ac[i];
@@ -1351,6 +1370,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         }
         if (tid == 0) a.ucount[wk] = n;
         __syncthreads();
+        }
     }
 }
 
