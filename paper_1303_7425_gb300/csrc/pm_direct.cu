@@ -1206,6 +1206,7 @@ struct HashArgs {
     const u64 *wlo, *whi;        // the round's windows (rank bounds)
     u32 nwin;
     u32 *E2;                     // per CTA: column ranges of rows in its last window, 2 * na words (by row)
+    u32 *RL;                     // per CTA: the window's rows with products, thread t's k-th at t + DT k (na + DT words)
     u64 *okey, *ocoef;           // window w's terms at w * HT (coefficient words: words)
     u64 *ucount;                 // terms of window w, or HFAILED
     u32 *wnext;                  // window counter
@@ -1231,6 +1232,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (a.abort && *a.abort) return;
     u32 *E2 = a.E2 + (size_t)blockIdx.x * 2 * a.na;
+    u32 *RL = a.RL + (size_t)blockIdx.x * (a.na + DT);
     const u64 bmin = a.B[0], bmax = a.B[a.nb - 1];
     for (u32 x = tid; x < HT; x += DT) {
         keys[x] = HEMPTY;
@@ -1260,7 +1262,9 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         __syncthreads();
         const u32 i0 = s_rows[0], i1 = s_rows[1];
         // FindEdge for both boundaries: each row's edges rise from its edge
-        // at the last window's top (0 for rows new to this CTA)
+        // at the last window's top (0 for rows new to this CTA); the thread
+        // lists its rows that have products in the window
+        u32 nrows = 0;
         for (u32 r = i0 + tid; r < i1; r += DT) {
             const u64 ar = a.A[r];
             const u32 js = r < pi1 ? E2[2 * r + 1] : 0u;
@@ -1268,18 +1272,19 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
             const u32 jh = gallop_up_k(a.B, a.nb, js, hi > ar ? hi - ar : 0);
             E2[2 * r] = jl;
             E2[2 * r + 1] = jh;
+            if (jh > jl) RL[tid + DT * nrows++] = r;
         }
         if (i1 > pi1) pi1 = i1;
         __syncthreads();
-        // the products: each thread takes rows i0 + tid, i0 + tid + DT, ...
-        // and inserts its row's products (a window in a sparse box has few
-        // products per row, so staging rows through shared memory and
-        // balancing them across the block costs more than it saves)
+        // the products: each thread inserts the products of its listed rows
+        // (a window in a sparse box has few products per row, so staging
+        // rows through shared memory and balancing them across the block
+        // costs more than it saves)
         const volatile u32 *over = &s_over;
-        for (u32 i = i0 + tid; i < i1; i += DT) {
+        for (u32 k = 0; k < nrows; k++) {
             if (*over) break;
+            const u32 i = RL[tid + DT * k];
             const u32 jl = E2[2 * i], jh = E2[2 * i + 1];
-            if (jh <= jl) continue;
             const u32 ra = (u32)a.A[i] - (u32)lo;
             const u64 ca = a.Ac[i];
             for (u32 j = jl; j < jh; j++) {
@@ -1433,6 +1438,7 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     };
     std::vector<Done> done;
     u32 *E2 = S.get<u32>((size_t)c.sm_count * 2 * in.na);
+    u32 *RL = S.get<u32>((size_t)c.sm_count * (in.na + DT));
     const size_t smem = HASH_SMEM(acc_bytes(acc));
     u32 rounds = 0;
     while (!wl.empty()) {
@@ -1458,6 +1464,7 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         h.whi = dhi;
         h.nwin = nw;
         h.E2 = E2;
+        h.RL = RL;
         h.okey = skey;
         h.ocoef = scoef;
         h.ucount = cnt;
