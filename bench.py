@@ -83,7 +83,9 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
-    ap.add_argument("--workload", default="sparse5v", choices=["sparse5v", "dense4v", "sparse4v", "batch"],
+    ap.add_argument("--shard", action="store_true",
+                    help="one product split over the ranks by output key range (Alg. 2) instead of replicas")
+    ap.add_argument("--workload", default="sparse5v", choices=["sparse5v", "dense4v", "sparse4v", "batch", "paper_ex2", "paper_ex3"],
                     help="what the timed steps run; the line reports that workload (default: the largest)")
     ap.add_argument("--batch-count", type=int, default=4096, help="products of the batched workload")
     ap.add_argument("--serving-count", type=int, default=3000, help="requests of the serving workload")
@@ -460,6 +462,38 @@ def _device_product(torch, np, w, cap=None):
     return dict(field_bits=w.field_bits, kind=w.kind, f_exps=f[0], f_coefs=f[1], g_exps=g[0], g_coefs=g[1], out=out)
 
 
+def bench_paper_example(P, torch, nm, peak=None):
+    """The paper's Example 2 or 3 (Sec. 6) at full size, mod p, through
+    pm_polymul (hashed windows): one warm call, then the mean of two."""
+    import numpy as np
+
+    import polygen
+    ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
+           "ex3": "Fermi GPU, FP64: 129 s; 64 Xeon cores, integers: 29.7 s (Sec. 6)"}
+    wx = polygen.paper_example(nm)
+    fx, gx = _dev(torch, np, wx.f), _dev(torch, np, wx.g)
+    capx = {"ex2": 312855140, "ex3": 144049555}[nm] + 16
+    outx = (torch.empty(capx, dtype=torch.int64, device="cuda"),
+            torch.empty(capx, dtype=torch.int64, device="cuda"))
+    P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+    tx = []
+    for _ in range(2):
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record()
+        rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+        b_.record()
+        torch.cuda.synchronize()
+        tx.append(a_.elapsed_time(b_))
+    value = wx.term_products / (statistics.mean(tx) * 1e-3)
+    res = {"value": value, "unit": UNIT, "ms_per_step": statistics.mean(tx), "n_out": rx.n,
+           "term_products": wx.term_products, "strategy": rx.stats["strategy"],
+           "window_rounds": rx.stats["refine_rounds"], "window_runs": rx.stats["n_ranges"],
+           "workload": wx.note, "paper_context": ctx[nm], "frac": value / peak if peak else None}
+    del fx, gx, outx
+    torch.cuda.empty_cache()
+    return res
+
+
 def bench_batched(P, torch, count, tune=True):
     """The batched workload: `count` independent sparse products -- one captured batched pass
     versus one pm_polymul launch per product, on the same GPU."""
@@ -665,6 +699,9 @@ def run_ours(args):
     if args.workload == "batch":  # profiling aid: the batched pass as the timed step
         print(json.dumps(bench_batched(P, torch, args.batch_count, tune=not args.no_tune)))
         return
+    if args.workload in ("paper_ex2", "paper_ex3"):  # profiling aid: the paper's Example 2 or 3
+        print(json.dumps(bench_paper_example(P, torch, args.workload[6:])))
+        return
     name = args.workload
     w = _workload(name)
     products = w.term_products
@@ -794,31 +831,8 @@ def secondary_workloads(extras, P, torch, np, polygen, args, name, flush, op, pr
             "frac": we.term_products / (statistics.mean(pe[0]) * 1e-3) / op["peak"],
             "paper_context": "Fermi GPU, FP64 coefficients: 32 s; 64 Xeon cores, integers: 16.1 s (Sec. 6)"}
     # Examples 2 and 3 (hashed windows)
-    ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
-           "ex3": "Fermi GPU, FP64: 129 s; 64 Xeon cores, integers: 29.7 s (Sec. 6)"}
     for nm in ("ex2", "ex3"):
-        wx = polygen.paper_example(nm)
-        fx, gx = _dev(torch, np, wx.f), _dev(torch, np, wx.g)
-        capx = {"ex2": 312855140, "ex3": 144049555}[nm] + 16
-        outx = (torch.empty(capx, dtype=torch.int64, device="cuda"),
-                torch.empty(capx, dtype=torch.int64, device="cuda"))
-        P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
-        tx = []
-        for _ in range(2):
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record()
-            rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
-            b_.record()
-            torch.cuda.synchronize()
-            tx.append(a_.elapsed_time(b_))
-        extras["paper_" + nm] = {
-            "value": wx.term_products / (statistics.mean(tx) * 1e-3), "unit": UNIT,
-            "ms_per_step": statistics.mean(tx), "n_out": rx.n, "term_products": wx.term_products,
-            "strategy": rx.stats["strategy"], "window_rounds": rx.stats["refine_rounds"],
-            "workload": wx.note, "paper_context": ctx[nm],
-            "frac": wx.term_products / (statistics.mean(tx) * 1e-3) / op["peak"]}
-        del fx, gx, outx
-        torch.cuda.empty_cache()
+        extras["paper_" + nm] = bench_paper_example(P, torch, nm, op["peak"])
     extras["sparse5v_20000x20000"] = bench_sparse_large(P, torch, np, polygen, flush)
     sb = bench_batched(P, torch, args.batch_count, tune=not args.no_tune)
     extras["sparse_batch_4096"] = sb
@@ -831,10 +845,74 @@ def secondary_workloads(extras, P, torch, np, polygen, args, name, flush, op, pr
     extras["serving_mix"] = bench_serving(P, torch, args.serving_count, rate, tune=not args.no_tune)
 
 
+def run_sharded(args):
+    """One product over all ranks (Alg. 2, Sec. 3): every rank computes the
+    same split of the output key space, multiplies its slice and the slices
+    are gathered in rank order (paper_1303_7425_gb300.shard.sharded_polymul).
+    The whole job makes the product once per step, so the scaling is strong;
+    value = the product's term products / the slowest rank's step time."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1303_7425_gb300 as P
+    from paper_1303_7425_gb300.shard import sharded_polymul
+    rank, local, world = env_rank()
+    # a one-rank group when started without torchrun
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    os.environ.setdefault("MASTER_PORT", "29531")
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", rank=rank, world_size=world, device_id=torch.device("cuda", local))
+    P.lib()  # fails loudly if the CUDA library is missing
+    name = args.workload if args.workload in WORKLOADS else "sparse5v"
+    w = _workload(name)
+    f, g = _dev(torch, np, w.f), _dev(torch, np, w.g)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    run = lambda: sharded_polymul(w.field_bits, f[0], f[1], g[0], g[1])
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    t0 = time.time()
+    ts = []
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        dist.barrier()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        hk, hc, n, st = run()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1)
+    ms_step = max_over_ranks(statistics.mean(ts), dist, "cuda")
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": w.term_products / (ms_step * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "u64 mod 2^61-1", "data": "synthetic",
+            "config": {"workload": WORKLOADS[name], "term_products": w.term_products,
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)",
+                       "api": "shard.sharded_polymul: pm_shard_bounds, pm_polymul_range on each rank, "
+                              "then the ordered all-gather of the slices",
+                       "parallelism": f"key-range shards x{world}"},
+            "roofline": None, "cpu_baseline": None, "e2e": None,
+            "gpu_launches": args.steps * st["kernel_launches"],
+            "gpu_launches_note": "the slice's pm_polymul_range kernels per step; the split's are not counted",
+            "clocks": clocks, "n_out": n,
+            "slice": {"products": st["slice_products"], "terms": st["slice_terms"]}}))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_sharded(args)
     else:
         run_ours(args)
 
