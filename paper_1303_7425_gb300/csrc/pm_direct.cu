@@ -1410,9 +1410,10 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     const u32 words = kind == PM_COEF_M61 ? 1 : (kind == PM_COEF_I64_ACC192 ? 3 : 2);
     const int acc = acc_policy(kind, in.na < in.nb ? in.na : in.nb, requested);
     // first windows: cost-balanced by term products (no window terms),
-    // about products / (HT 256) of them, at least 4 per SM; then no window
-    // wider than 2^31 ranks
-    u64 G0 = products / ((u64)HT * 256);
+    // about products / (4 HT) of them (at most 2^20), at least 4 per SM;
+    // then no window wider than 2^31 ranks.  Small first windows overflow
+    // less often, and an overflowing window's inserted products are lost
+    u64 G0 = products / ((u64)HT * 4);
     if (G0 < (u64)c.sm_count * 4) G0 = (u64)c.sm_count * 4;
     if (G0 > end - lo) G0 = end - lo;
     if (G0 > (1u << 20)) G0 = 1u << 20;
