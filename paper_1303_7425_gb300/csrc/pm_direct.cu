@@ -1193,7 +1193,7 @@ void launch_direct(Ctx &c, Scratch &S, DirectArgs &a, u32 slots, int kind, int r
 // ---------------------------------------------------------------------------
 
 constexpr u32 HT = 4096, HT_BITS = 12;
-constexpr u32 HWIN_RUN = 8;   // consecutive windows a CTA takes at a time
+constexpr u32 HWIN_RUN = 16;  // consecutive windows a CTA takes at a time
 // a window may fill 3968 of the 4096 slots (probe runs up to 256): fewer,
 // fuller windows beat shorter probe runs here
 constexpr u32 HT_LOAD = 3968;
