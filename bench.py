@@ -83,6 +83,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the secondary workloads")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="skip the autotuner (library defaults)")
+    ap.add_argument("--example-power", type=int, default=None,
+                    help="with --workload paper_ex2|paper_ex3: a smaller exponent than the paper's (profiling)")
     ap.add_argument("--shard", action="store_true",
                     help="one product split over the ranks by output key range (Alg. 2) instead of replicas")
     ap.add_argument("--workload", default="sparse5v", choices=["sparse5v", "dense4v", "sparse4v", "batch", "paper_ex2", "paper_ex3"],
@@ -462,25 +464,29 @@ def _device_product(torch, np, w, cap=None):
     return dict(field_bits=w.field_bits, kind=w.kind, f_exps=f[0], f_coefs=f[1], g_exps=g[0], g_coefs=g[1], out=out)
 
 
-def bench_paper_example(P, torch, nm, peak=None):
+def bench_paper_example(P, torch, nm, peak=None, power=None):
     """The paper's Example 2 or 3 (Sec. 6) at full size, mod p, through
-    pm_polymul (hashed windows): one warm call, then the mean of two."""
+    pm_polymul (hashed windows): one warm call, then the mean of two.  At a
+    smaller power (a profiling aid) the hashed windows are asked for, since
+    the library would pick the direct windows for the smaller box."""
     import numpy as np
 
     import polygen
     ctx = {"ex2": "Fermi GPU, FP64: 71 s; 64 Xeon cores, integers: 30.2 s (Sec. 6)",
            "ex3": "Fermi GPU, FP64: 129 s; 64 Xeon cores, integers: 29.7 s (Sec. 6)"}
-    wx = polygen.paper_example(nm)
+    wx = polygen.paper_example(nm, power)
     fx, gx = _dev(torch, np, wx.f), _dev(torch, np, wx.g)
-    capx = {"ex2": 312855140, "ex3": 144049555}[nm] + 16
+    capx = ({"ex2": 312855140, "ex3": 144049555}[nm] + 16 if power is None
+            else P.out_bound(wx.field_bits, fx[0], gx[0]))
     outx = (torch.empty(capx, dtype=torch.int64, device="cuda"),
             torch.empty(capx, dtype=torch.int64, device="cuda"))
-    P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+    strat = "auto" if power is None else "hash"
+    P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx, strategy=strat)
     tx = []
     for _ in range(2):
         a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a_.record()
-        rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx)
+        rx = P.polymul(wx.field_bits, fx[0], fx[1], gx[0], gx[1], out=outx, strategy=strat)
         b_.record()
         torch.cuda.synchronize()
         tx.append(a_.elapsed_time(b_))
@@ -700,7 +706,7 @@ def run_ours(args):
         print(json.dumps(bench_batched(P, torch, args.batch_count, tune=not args.no_tune)))
         return
     if args.workload in ("paper_ex2", "paper_ex3"):  # profiling aid: the paper's Example 2 or 3
-        print(json.dumps(bench_paper_example(P, torch, args.workload[6:])))
+        print(json.dumps(bench_paper_example(P, torch, args.workload[6:], power=args.example_power)))
         return
     name = args.workload
     w = _workload(name)

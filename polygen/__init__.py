@@ -215,29 +215,35 @@ def paper_example1() -> Workload:
                     "f1 = (1+x+y+z+t)^40, g1 = f1 + 1 (135,751 terms each)")
 
 
-def paper_example(name: str) -> Workload:
+def paper_example(name: str, power: Optional[int] = None) -> Workload:
     """Sec. 6, Examples 1-3, coefficients mod 2^61 - 1 (multinomial
     expansions; no random draws):
       ex1: (1+x+y+z+t)^40 times itself plus one (4 variables);
       ex2: (1+x+y+2z^2+3t^3+5u^5)^25 times (1+u+t+2z^2+3y^3+5x^5)^25;
       ex3: (1+u^2+v+w^2+x-y^2)^28 times (1+u+v^2+w+x^2+y^3)^28 + 1.
-    Variables in the order written (x_1 first)."""
+    Variables in the order written (x_1 first).  `power` (Examples 2 and 3
+    only) replaces the paper's exponent 25 or 28 by a smaller one: the same
+    shape at a size that profiles quickly."""
     if name == "ex1":
         return paper_example1()
     if name == "ex2":
-        fe, fcl = multinomial_power(5, 25, [(1, 1), (1, 1), (2, 2), (3, 3), (5, 5)])
-        ge, gcl = multinomial_power(5, 25, [(5, 5), (3, 3), (2, 2), (1, 1), (1, 1)])
+        k = 25 if power is None else power
+        fe, fcl = multinomial_power(5, k, [(1, 1), (1, 1), (2, 2), (3, 3), (5, 5)])
+        ge, gcl = multinomial_power(5, k, [(5, 5), (3, 3), (2, 2), (1, 1), (1, 1)])
         bits = [12] * 5                     # exponents up to 150 per variable
-        desc = "(1+x+y+2z^2+3t^3+5u^5)^25 x (1+u+t+2z^2+3y^3+5x^5)^25"
+        desc = f"(1+x+y+2z^2+3t^3+5u^5)^{k} x (1+u+t+2z^2+3y^3+5x^5)^{k}"
     elif name == "ex3":
-        fe, fcl = multinomial_power(5, 28, [(1, 2), (1, 1), (1, 2), (1, 1), (-1, 2)])
-        ge, gcl = multinomial_power(5, 28, [(1, 1), (1, 2), (1, 1), (1, 2), (1, 3)])
+        k = 28 if power is None else power
+        fe, fcl = multinomial_power(5, k, [(1, 2), (1, 1), (1, 2), (1, 1), (-1, 2)])
+        ge, gcl = multinomial_power(5, k, [(1, 1), (1, 2), (1, 1), (1, 2), (1, 3)])
         const = int(np.flatnonzero((ge == 0).all(axis=1))[0])
         gcl[const] = (gcl[const] + 1) % P61
         bits = [12] * 5                     # exponents up to 140 per variable
-        desc = "(1+u^2+v+w^2+x-y^2)^28 x ((1+u+v^2+w+x^2+y^3)^28 + 1)"
+        desc = f"(1+u^2+v+w^2+x-y^2)^{k} x ((1+u+v^2+w+x^2+y^3)^{k} + 1)"
     else:
         raise ValueError(name)
+    if k > (25 if name == "ex2" else 28) or k < 1:
+        raise ValueError("power above the paper's or below 1")
     f = Poly(fe, np.array(fcl, dtype=np.uint64))
     g = Poly(ge, np.array(gcl, dtype=np.uint64))
     return Workload(f"paper_{name}", 5, bits, "m61", f, g, desc)
