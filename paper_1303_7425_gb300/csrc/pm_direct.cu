@@ -1208,7 +1208,7 @@ struct HashArgs {
     const u64 *wlo, *whi;        // the round's windows (rank bounds)
     u32 nwin;
     u32 *E2;                     // per CTA: column ranges of rows in its last window, 2 * na words (by row)
-    u32 *RL;                     // per CTA: the window's rows with products, thread t's k-th at t + DT k (na + DT words)
+    u32 *RL;                     // per CTA: the window's rows with products, in any order (na words)
     u64 *okey, *ocoef;           // window w's terms at w * HT (coefficient words: words)
     u64 *ucount;                 // terms of window w, or HFAILED
     u32 *wnext;                  // window counter
@@ -1222,7 +1222,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ u64 ws[32];
-    __shared__ u32 s_next, s_count, s_over, s_rows[2];
+    __shared__ u32 s_next, s_count, s_over, s_rows[2], s_nlist, s_take;
     using HA = Acc<ACC, HT>;
     u32 *keys = (u32 *)smem;
     HA acc;
@@ -1257,6 +1257,8 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         if (tid == 0) {
             s_count = 0;
             s_over = 0;
+            s_nlist = 0;
+            s_take = 0;
             // rows reaching the window, from the last window's rows
             s_rows[0] = lo > bmax ? gallop_up_k(a.A, a.na, s_rows[0], lo - bmax) : s_rows[0];
             s_rows[1] = hi > bmin ? gallop_up_k(a.A, a.na, s_rows[1], hi - bmin) : s_rows[1];
@@ -1266,30 +1268,48 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         // FindEdge for both boundaries: each row's edges rise from its edge
         // at the last window's top (0 for rows new to this CTA); the thread
         // lists its rows that have products in the window
-        u32 nrows = 0;
-        for (u32 r = i0 + tid; r < i1; r += DT) {
-            const u64 ar = a.A[r];
-            const u32 js = r < pi1 ? E2[2 * r + 1] : 0u;
-            const u32 jl = gallop_up_k(a.B, a.nb, js, lo > ar ? lo - ar : 0);
-            const u32 jh = gallop_up_k(a.B, a.nb, js, hi > ar ? hi - ar : 0);
-            E2[2 * r] = jl;
-            E2[2 * r + 1] = jh;
-            if (jh > jl) RL[tid + DT * nrows++] = r;
+        // (the warp's rows with products are appended to the list with one
+        // atomic per warp and step)
+        for (u32 r0 = i0 + (tid & ~31u); r0 < i1; r0 += DT) {
+            const u32 r = r0 + lane;
+            bool has = false;
+            if (r < i1) {
+                const u64 ar = a.A[r];
+                const u32 js = r < pi1 ? E2[2 * r + 1] : 0u;
+                const u32 jl = gallop_up_k(a.B, a.nb, js, lo > ar ? lo - ar : 0);
+                const u32 jh = gallop_up_k(a.B, a.nb, js, hi > ar ? hi - ar : 0);
+                E2[2 * r] = jl;
+                E2[2 * r + 1] = jh;
+                has = jh > jl;
+            }
+            const u32 bal = __ballot_sync(0xffffffffu, has);
+            u32 at = 0;
+            if (lane == 0 && bal) at = atomicAdd(&s_nlist, (u32)__popc(bal));
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (has) RL[at + __popc(bal & ((1u << lane) - 1u))] = r;
         }
         if (i1 > pi1) pi1 = i1;
         __syncthreads();
-        // the products: each thread inserts the products of its listed rows
-        // (a window in a sparse box has few products per row, so staging
-        // rows through shared memory and balancing them across the block
-        // costs more than it saves)
+        // the products: warps take the listed rows from a counter, and the
+        // 32 lanes of a warp insert a row's products together (consecutive
+        // columns: coalesced loads, and no two lanes of one step share a
+        // monomial).  A window's rows hold tens of products each and very
+        // unevenly, so a thread per row would leave the block waiting for
+        // its busiest thread.
         const volatile u32 *over = &s_over;
-        for (u32 k = 0; k < nrows; k++) {
-            if (*over) break;
-            const u32 i = RL[tid + DT * k];
+        const u32 nlist = s_nlist;
+        constexpr u32 TAKE = 4;  // rows per claim
+        for (;;) {
+            u32 t0 = 0;
+            if (lane == 0) t0 = *over ? nlist : atomicAdd(&s_take, TAKE);
+            t0 = __shfl_sync(0xffffffffu, t0, 0);
+            if (t0 >= nlist) break;
+            for (u32 t = t0; t < min(t0 + TAKE, nlist); t++) {
+            const u32 i = RL[t];
             const u32 jl = E2[2 * i], jh = E2[2 * i + 1];
             const u32 ra = (u32)a.A[i] - (u32)lo;
             const u64 ca = a.Ac[i];
-            for (u32 j = jl; j < jh; j++) {
+            for (u32 j = jl + lane; j < jh; j += 32) {
                 const u32 key = ra + __ldg(a.B32 + j);  // rank - lo, below span
                 const u64 gc = __ldg(a.Bc + j);
                 // linear probing from a multiplicative hash of the rank
@@ -1313,12 +1333,12 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
                     }
                     h = (h + 1) & (HT - 1);
                 }
-                if (done) {
-                    acc.add(h, ca, gc);
-                } else {
+                if (!done) {
                     s_over = 1;
                     break;
                 }
+                acc.add(h, ca, gc);
+            }
             }
         }
         __syncthreads();
