@@ -1207,8 +1207,8 @@ struct HashArgs {
     u32 na, nb;
     const u64 *wlo, *whi;        // the round's windows (rank bounds)
     u32 nwin;
-    u32 *E2;                     // per CTA: column ranges of rows in its last window, 2 * na words (by row)
-    u32 *RL;                     // per CTA: the window's rows with products, in any order (na words)
+    u32 *E2;                     // per CTA: each row's upper column edge in its last window (na words, by row)
+    u32 *RL;                     // per CTA: the window's rows with products and their lower edges, in any order (2 na words)
     u64 *okey, *ocoef;           // window w's terms at w * HT (coefficient words: words)
     u64 *ucount;                 // terms of window w, or HFAILED
     u32 *wnext;                  // window counter
@@ -1233,8 +1233,8 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
     u32 *hist = (u32 *)(iB + HT);  // HT_HIST words
     const u32 tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (a.abort && *a.abort) return;
-    u32 *E2 = a.E2 + (size_t)blockIdx.x * 2 * a.na;
-    u32 *RL = a.RL + (size_t)blockIdx.x * (a.na + DT);
+    u32 *E2 = a.E2 + (size_t)blockIdx.x * a.na;
+    u32 *RL = a.RL + (size_t)blockIdx.x * 2 * a.na;
     const u64 bmin = a.B[0], bmax = a.B[a.nb - 1];
     for (u32 x = tid; x < HT; x += DT) {
         keys[x] = HEMPTY;
@@ -1273,20 +1273,27 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         for (u32 r0 = i0 + (tid & ~31u); r0 < i1; r0 += DT) {
             const u32 r = r0 + lane;
             bool has = false;
+            u32 jl = 0;
             if (r < i1) {
                 const u64 ar = a.A[r];
-                const u32 js = r < pi1 ? E2[2 * r + 1] : 0u;
-                const u32 jl = gallop_up_k(a.B, a.nb, js, lo > ar ? lo - ar : 0);
+                const bool known = r < pi1;
+                const u32 js = known ? E2[r] : 0u;
+                jl = gallop_up_k(a.B, a.nb, js, lo > ar ? lo - ar : 0);
                 const u32 jh = gallop_up_k(a.B, a.nb, js, hi > ar ? hi - ar : 0);
-                E2[2 * r] = jl;
-                E2[2 * r + 1] = jh;
+                // most rows have no product in the window and keep their
+                // edge: no store for them
+                if (jh != js || !known) E2[r] = jh;
                 has = jh > jl;
             }
             const u32 bal = __ballot_sync(0xffffffffu, has);
             u32 at = 0;
             if (lane == 0 && bal) at = atomicAdd(&s_nlist, (u32)__popc(bal));
             at = __shfl_sync(0xffffffffu, at, 0);
-            if (has) RL[at + __popc(bal & ((1u << lane) - 1u))] = r;
+            if (has) {
+                const u32 x = at + __popc(bal & ((1u << lane) - 1u));
+                RL[2 * x] = r;
+                RL[2 * x + 1] = jl;
+            }
         }
         if (i1 > pi1) pi1 = i1;
         __syncthreads();
@@ -1305,8 +1312,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
             t0 = __shfl_sync(0xffffffffu, t0, 0);
             if (t0 >= nlist) break;
             for (u32 t = t0; t < min(t0 + TAKE, nlist); t++) {
-            const u32 i = RL[t];
-            const u32 jl = E2[2 * i], jh = E2[2 * i + 1];
+            const u32 i = RL[2 * t], jl = RL[2 * t + 1], jh = E2[i];
             const u32 ra = (u32)a.A[i] - (u32)lo;
             const u64 ca = a.Ac[i];
             for (u32 j = jl + lane; j < jh; j += 32) {
@@ -1460,8 +1466,8 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         const u64 *k, *cf;
     };
     std::vector<Done> done;
-    u32 *E2 = S.get<u32>((size_t)c.sm_count * 2 * in.na);
-    u32 *RL = S.get<u32>((size_t)c.sm_count * (in.na + DT));
+    u32 *E2 = S.get<u32>((size_t)c.sm_count * in.na);
+    u32 *RL = S.get<u32>((size_t)c.sm_count * 2 * in.na);
     const size_t smem = HASH_SMEM(acc_bytes(acc));
     u32 rounds = 0;
     while (!wl.empty()) {
