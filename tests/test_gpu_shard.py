@@ -94,3 +94,31 @@ def test_arbitrary_key_slices(strategy):
         np.testing.assert_array_equal(cc.reshape(-1), np.asarray(c, dtype=np.uint64)[sel])
     empty = P.polymul_range(w.field_bits, f[0], f[1], g[0], g[1], int(keys[-1]) + 1, 2**64 - 1, strategy=strategy)
     assert empty.n == 0
+
+
+def test_sharded_polymul_one_rank_group_equals_the_product():
+    """shard.sharded_polymul (the split, this rank's slice, the ordered
+    gather) on a one-rank gloo group: the gathered result equals pm_polymul
+    bit for bit, for both coefficient kinds."""
+    import socket
+
+    import torch.distributed as dist
+
+    import paper_1303_7425_gb300 as P
+    from paper_1303_7425_gb300.shard import sharded_polymul
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        for name in ("sparse4v", "dense4v_i64"):
+            w, _ = _cases()[name]
+            f = to_dev(w.f.exps, w.f.coefs, w.kind)
+            g = to_dev(w.g.exps, w.g.coefs, w.kind)
+            hk, hc, n, st = sharded_polymul(w.field_bits, f[0], f[1], g[0], g[1], kind=w.kind)
+            whole = P.polymul(w.field_bits, f[0], f[1], g[0], g[1], kind=w.kind)
+            assert n == whole.n and st["slice_terms"] == whole.n
+            np.testing.assert_array_equal(hk.numpy(), whole.keys.cpu().numpy())
+            np.testing.assert_array_equal(hc.numpy().reshape(-1), whole.coefs.cpu().numpy().reshape(-1))
+    finally:
+        dist.destroy_process_group()
