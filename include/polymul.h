@@ -114,7 +114,8 @@ typedef struct pm_terms_out {
 /* Tuning knobs; pass NULL (or zeros) for the autotuned defaults. */
 /* Direct strategy accumulators (mod p kind). */
 #define PM_ACC_AUTO   0  /* direct: three limbs; hash: limbs when
-                            min(n_f, n_g) <= 65537, else wide                   */
+                            min(n_f, n_g) <= 65537, else wide, with the limbs
+                            in windows of at most 65537 rows with products   */
 #define PM_ACC_WIDE   1  /* 64-bit sum + 32-bit wrap count per slot             */
 #define PM_ACC_LIMBS  2  /* four 16-bit limbs in 32-bit counters per slot       */
 #define PM_ACC_LIMBS3 3  /* direct: three limbs (22, 21, 21 bits) in 32-bit

@@ -1214,6 +1214,7 @@ struct HashArgs {
     u32 *wnext;                  // window counter
     Layout L;
     u32 words;
+    u32 mixed;                   // wide accumulator chosen by the library: windows may use the limbs
     const u32 *abort;
 };
 
@@ -1224,10 +1225,21 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
     __shared__ u64 ws[32];
     __shared__ u32 s_next, s_count, s_over, s_rows[2], s_nlist, s_take;
     using HA = Acc<ACC, HT>;
+    // when the library chose the wide accumulator (operands above 65537
+    // terms), a window switches to the four-limb one if at most 65537 rows
+    // have products in it: a slot takes at most one product per row, so the
+    // limb counters cannot overflow, and their fire-and-forget reductions
+    // are cheaper than the wide one's returned add.  Both lay out on the
+    // same 16 bytes per slot.
+    constexpr bool HYB = ACC == ACC_W64;
+    using HL = Acc<ACC_L16, HT>;
+    constexpr u32 SLOT_B = HYB ? HL::bytes : HA::bytes;
     u32 *keys = (u32 *)smem;
     HA acc;
+    HL acc16;
     acc.carve(smem + HT * 4);
-    unsigned char *sb_ = smem + HT * 4 + (size_t)HT * HA::bytes;
+    acc16.carve(smem + HT * 4);
+    unsigned char *sb_ = smem + HT * 4 + (size_t)HT * SLOT_B;
     u64 *kA = (u64 *)sb_, *kB = kA + HT;
     uint16_t *iA = (uint16_t *)(kB + HT), *iB = iA + HT;
     u32 *hist = (u32 *)(iB + HT);  // HT_HIST words
@@ -1236,9 +1248,14 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
     u32 *E2 = a.E2 + (size_t)blockIdx.x * a.na;
     u32 *RL = a.RL + (size_t)blockIdx.x * 2 * a.na;
     const u64 bmin = a.B[0], bmax = a.B[a.nb - 1];
+    // clear a slot: in the mixed case every byte of its 16 (both layouts)
+    auto zero_slot = [&](u32 x) {
+        if (HYB) acc16.zero(x);
+        else acc.zero(x);
+    };
     for (u32 x = tid; x < HT; x += DT) {
         keys[x] = HEMPTY;
-        acc.zero(x);
+        zero_slot(x);
     }
     if (tid == 0) {
         s_rows[0] = 0;
@@ -1305,6 +1322,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         // its busiest thread.
         const volatile u32 *over = &s_over;
         const u32 nlist = s_nlist;
+        const bool limbs = HYB && a.mixed && nlist <= 65537;
         constexpr u32 TAKE = 4;  // rows per claim
         for (;;) {
             u32 t0 = 0;
@@ -1343,7 +1361,8 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
                     s_over = 1;
                     break;
                 }
-                acc.add(h, ca, gc);
+                if (limbs) acc16.add(h, ca, gc);
+                else acc.add(h, ca, gc);
             }
             }
         }
@@ -1352,7 +1371,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
             // abandoned: report it, clear the table for the next window
             for (u32 x = tid; x < HT; x += DT) {
                 keys[x] = HEMPTY;
-                acc.zero(x);
+                zero_slot(x);
             }
             if (tid == 0) a.ucount[wk] = HFAILED;
             __syncthreads();
@@ -1366,7 +1385,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         for (u32 q = 0; q < PER; q++) {
             const u32 x = tid * PER + q;
             u64 v0, v1, v2;
-            if (keys[x] != HEMPTY && acc.finalize(x, v0, v1, v2)) {
+            if (keys[x] != HEMPTY && (limbs ? acc16.finalize(x, v0, v1, v2) : acc.finalize(x, v0, v1, v2))) {
                 nzf |= 1u << q;
                 mine++;
             }
@@ -1389,7 +1408,8 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         for (u32 q = tid; q < n; q += DT) {
             const u32 x = iA[q];
             u64 v0, v1, v2;
-            acc.take(x, v0, v1, v2);
+            if (limbs) acc16.take(x, v0, v1, v2);
+            else acc.take(x, v0, v1, v2);
             a.okey[obase + q] = rank_to_key(a.L, lo + kA[q]);
             constexpr u32 W = HA::words;
             a.ocoef[W * (obase + q)] = v0;
@@ -1399,7 +1419,7 @@ __global__ void __launch_bounds__(DT, 1) k_hash(HashArgs a)
         __syncthreads();
         for (u32 x = tid; x < HT; x += DT) {
             keys[x] = HEMPTY;
-            acc.zero(x);
+            zero_slot(x);
         }
         if (tid == 0) a.ucount[wk] = n;
         __syncthreads();
@@ -1468,7 +1488,8 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
     std::vector<Done> done;
     u32 *E2 = S.get<u32>((size_t)c.sm_count * in.na);
     u32 *RL = S.get<u32>((size_t)c.sm_count * 2 * in.na);
-    const size_t smem = HASH_SMEM(acc_bytes(acc));
+    // the wide accumulator's windows may use the four-limb layout (16 bytes)
+    const size_t smem = HASH_SMEM(acc == ACC_W64 ? 16u : acc_bytes(acc));
     u32 rounds = 0;
     while (!wl.empty()) {
         if (++rounds > 40) throw Error(PM_ECUDA, "hash windows did not converge");
@@ -1500,6 +1521,7 @@ u64 hash_product(Ctx &c, Scratch &S, const HashInputs &in, int kind, int request
         h.wnext = wnext;
         h.L = in.L;
         h.words = words;
+        h.mixed = acc == ACC_W64 && requested != PM_ACC_WIDE ? 1u : 0u;
         const unsigned grid = (unsigned)std::min<u64>(nw, (u64)c.sm_count);
         if (acc == ACC_W64) {
             set_smem(k_hash<ACC_W64>, smem);

@@ -305,6 +305,23 @@ def test_hash_strategy_exact(case):
     assert_same(gpu, ref, w.field_bits)
 
 
+@pytest.mark.parametrize("case", ["sparse5", "colliding"])
+def test_hash_wide_accumulator_exact(case):
+    """Hashed windows with the wide accumulator asked for (a 64-bit sum and
+    its wrap count per slot, the one the library picks for operands above
+    65537 terms, whose windows otherwise switch to the limbs): bit-exact
+    with the oracle, also over the splits of overflowing windows."""
+    if case == "sparse5":
+        w = polygen.sparse_product(polygen.Stream(9, 0), 5, 1500, 900, 30)
+    else:
+        w = polygen.sparse_product(polygen.Stream(12, 0), 3, 2000, 2000, 400)
+    ref = _oracle(w)
+    gpu = run_gpu(w.field_bits, w.kind, w.f.exps, w.f.coefs, w.g.exps, w.g.coefs, strategy="hash",
+                  accumulator="wide")
+    assert gpu[2]["strategy"] == "hash"
+    assert_same(gpu, ref, w.field_bits)
+
+
 def test_hash_windows_split_when_full():
     """4 million term products, nearly all distinct, over a box of 5e8 ranks:
     the first windows (about 6,600 monomials each) overflow their tables,
