@@ -102,7 +102,7 @@ typedef struct pm_terms_out {
 #define PM_STRATEGY_DIRECT 1  /* direct-addressed shared-memory accumulation       */
 #define PM_STRATEGY_SORT   2  /* shared-memory radix sort + segmented reduce       */
 #define PM_STRATEGY_HASH   3  /* hashed windows: a shared-memory hash table per
-                                 window of up to 2^32 ranks (sparse results in
+                                 window of up to 2^31 ranks (sparse results in
                                  large boxes)                                      */
 #define PM_STRATEGY_BUCKET 4  /* every term product written to a bucket of the
                                  output key space (two passes over the
